@@ -1,0 +1,163 @@
+/*
+ * jz.h -- C ABI of the GB300 stage-residual / Runge-Kutta library for the
+ * JAZzY-style compressible LES solver (arXiv 2003.08746).
+ *
+ * The library advances the five conserved variables Q = [rho, rho u, rho v,
+ * rho w, e] of the filtered Navier-Stokes equations (paper Sec. "Large Eddy
+ * Simulation Formulation", eqs. les, vec-les, con-prop, rhs) on one
+ * structured curvilinear (i, j, k) grid on one GPU, with the explicit
+ * 5-stage Runge-Kutta scheme of Algorithm 2.
+ *
+ * Conventions common to every entry point
+ *  - Every function returns an int status: JZ_OK (0) or a negative JZ_ERR_*
+ *    code.  No function aborts the process.  jz_last_error() gives a
+ *    thread-local message for the last failure on the calling thread.
+ *  - Arrays passed in or out are FP64, structure-of-arrays, C order
+ *    [var][nk][nj][ni] with i fastest, no ghost points.  N = ni * nj * nk.
+ *  - Array pointers may be host or device pointers (CUDA unified
+ *    addressing decides).  The caller owns them; the library never keeps
+ *    them after the call returns.  Host transfers finish before the call
+ *    returns; device transfers are ordered on the solver's stream.
+ *  - Handles (jz_grid, jz_solver) are owned by the library and freed by
+ *    the matching destroy call.  A grid must outlive the solvers built on it.
+ *  - All device work of a solver is issued on the stream given to
+ *    jz_create (NULL = legacy default stream).
+ *  - Non-dimensionalisation: rho_inf = a_inf = T_inf = 1, p_inf = 1/gamma,
+ *    lengths in jet diameters; mu_ref = mach_ref / Re.
+ */
+#ifndef JZ_H
+#define JZ_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define JZ_OK             0
+#define JZ_ERR_ARG       -1   /* invalid argument (sizes, pointers, flags)   */
+#define JZ_ERR_CUDA      -2   /* a CUDA runtime call failed                  */
+#define JZ_ERR_OOM       -3   /* device memory allocation failed             */
+#define JZ_ERR_NONFINITE -4   /* NaN/Inf or non-positive rho or p in state   */
+#define JZ_ERR_STATE     -5   /* call out of order (e.g. no metrics/state)   */
+
+/* ---- grid topologies --------------------------------------------------- */
+/* Triply periodic box: every node is advanced by the stencil; ghost points
+ * are periodic images (coordinates shifted by the period vectors). */
+#define JZ_TOPO_PERIODIC 1
+/* Cylindrical jet grid (paper Sec. LES Formulation, boundary conditions):
+ * i axial (i = 0 entrance, i = ni-1 exit), j radial (j = 0 on the jet axis,
+ * j = nj-1 far field), k azimuthal with nk unique periodic points (nk even).
+ * Nodes 1 <= i <= ni-2, 1 <= j <= nj-2 are advanced by the stencil; the
+ * others are set by the boundary conditions after every stage. */
+#define JZ_TOPO_JET      2
+
+/* ---- precision forms --------------------------------------------------- */
+#define JZ_PREC_FP64      0   /* every operation in FP64                      */
+#define JZ_PREC_FP32FLUX  1   /* fluxes, dissipation, SGS in FP32; state,
+                                 stage combination and totals in FP64        */
+
+#define JZ_N_MODES 8          /* azimuthal forcing modes m = 0..7            */
+#define JZ_N_FREQ  4          /* forcing frequencies (Strouhal numbers)      */
+
+typedef struct jz_grid jz_grid;
+typedef struct jz_solver jz_solver;
+
+/* Physical and numerical parameters (plain values).  Defaults used by the
+ * workloads: gamma 1.4, Pr 0.72, Pr_sgs 0.9 (paper eqs. q_mod, kappa_sgs),
+ * S1_K 110.4 K (eq. sutherland), T_ref_K 288.15, C_s 0.18, kappa2 1/4,
+ * kappa4 1/64, sigma 2/3, cfl 0.5. */
+typedef struct jz_params {
+    double gamma, Pr, Pr_sgs;
+    double Re;          /* Reynolds number built on U_ref = mach_ref * a_inf  */
+    double mach_ref;
+    double T_ref_K;     /* dimensional ambient temperature (Sutherland)      */
+    double S1_K;        /* Sutherland constant in kelvin                      */
+    double C_s;         /* Smagorinsky constant (0: no eddy viscosity)        */
+    double kappa2, kappa4, sigma;   /* Turkel-Vatsa dissipation constants     */
+    double cfl;         /* time step = cfl / max((l_xi + l_eta + l_zeta)/V)   */
+    double dt_fixed;    /* > 0: use this fixed time step instead              */
+    /* jet entrance (JZ_TOPO_JET only) */
+    double jet_mach;    /* U_j / a_inf                                        */
+    double theta_mom;   /* momentum thickness of the tanh profile (D)         */
+    double forcing_amp[JZ_N_MODES * JZ_N_FREQ];   /* A[m][f], m-major          */
+    double forcing_phi[JZ_N_MODES * JZ_N_FREQ];   /* azimuthal phase phi[m][f] */
+    double forcing_psi[JZ_N_MODES * JZ_N_FREQ];   /* temporal phase psi[m][f]  */
+    double strouhal[JZ_N_FREQ];
+    int precision;      /* JZ_PREC_FP64 or JZ_PREC_FP32FLUX                   */
+} jz_params;
+
+/* Per-call statistics returned by jz_rk_step. */
+typedef struct jz_step_stats {
+    double t;           /* time after the last step                           */
+    double dt;          /* time step of the last step                         */
+    double res_l2;      /* RMS over advanced nodes of RHS_rho at stage 1 of the last step */
+    double totals[5];   /* sum over all nodes of Q_m V (conservation totals)  */
+    double min_rho, min_p;
+    long long steps;    /* steps taken since jz_set_state                      */
+} jz_step_stats;
+
+/* Message of the last failure on this thread ("" if none).  Never NULL. */
+const char* jz_last_error(void);
+
+/* Library ABI version (increments when a signature changes). */
+int jz_version(void);
+
+/* Create a grid from node coordinates (paper Algorithm 2: Read(Mesh)).
+ *  xyz     [3][nk][nj][ni] Cartesian node coordinates, host or device.
+ *  period  [3][3] shift vectors of the i, j, k periods (JZ_TOPO_PERIODIC),
+ *          host memory; may be NULL for JZ_TOPO_JET (ignored there).
+ *  Sizes: JZ_TOPO_PERIODIC needs ni, nj, nk >= 1; JZ_TOPO_JET needs ni >= 4,
+ *  nj >= 4 and an even nk >= 4.  Ghost coordinates are built here (two
+ *  layers, paper Sec. "Parallel Implementation Aspects"): periodic images;
+ *  on the jet the azimuthal wrap, the across-axis mirror (i, m, k + nk/2)
+ *  and linear extrapolation beyond the far field and the entrance/exit.
+ *  Returns JZ_ERR_ARG on bad sizes/pointers, JZ_ERR_OOM, JZ_ERR_CUDA. */
+int jz_create_grid(int ni, int nj, int nk, const double* xyz, const double* period,
+                   int topology, jz_grid** out);
+int jz_destroy_grid(jz_grid* g);
+
+/* Compute the metrics of the curvilinear transformation (Algorithm 2:
+ * Calc(Jacob., Metric)): the area vectors S^xi = (xi_x, xi_y, xi_z)/J,
+ * S^eta, S^zeta in the symmetric conservative (Thomas-Lombard) form built
+ * from the centred index difference, and V = 1/J.  Runs on the default
+ * stream and synchronises.  Returns JZ_ERR_ARG if V <= 0 on a node the
+ * stencil advances (left-handed or degenerate grid). */
+int jz_compute_metrics(jz_grid* g);
+
+/* Copy the metrics to out [10][N] (host or device): S^xi_{x,y,z},
+ * S^eta_{x,y,z}, S^zeta_{x,y,z}, V.  JZ_ERR_STATE before jz_compute_metrics. */
+int jz_get_metrics(const jz_grid* g, double* out);
+
+/* Create a solver on a grid with computed metrics (Algorithm 2: Read(Input)).
+ *  stream  a cudaStream_t (may be NULL).  Allocates the state and the
+ *  scratch arrays of the chosen precision form on the device. */
+int jz_create(jz_grid* g, const jz_params* p, void* stream, jz_solver** out);
+int jz_destroy(jz_solver* s);
+
+/* Set the state Q (Algorithm 2: Calc(I.C.) / restart) and time t.  q is
+ * [5][N], host or device.  The state is taken as given (no boundary
+ * condition is applied); ghost points are filled. */
+int jz_set_state(jz_solver* s, const double* q, double t);
+
+/* Copy the current state to q [5][N], host or device. */
+int jz_get_state(jz_solver* s, double* q);
+
+/* One evaluation of RHS(q) of eq. vec-les (dQ/dt = -RHS) on every node the
+ * stencil advances; rhs [5][N] is 0 on the other nodes.  Does not touch the
+ * solver's state.  q and rhs host or device. */
+int jz_residual(jz_solver* s, const double* q, double* rhs);
+
+/* Advance nsteps time steps (Algorithm 2 main loop): for each of the 5
+ * stages, Q^(l) = Q^n - alpha_l dt RHS(Q^(l-1)), alpha = (1/4, 1/6, 3/8,
+ * 1/2, 1), then the boundary conditions and the ghost points.  dt is the
+ * CFL step of Q^n (or dt_fixed), kept on the device.  If out is non-NULL
+ * the statistics are computed and copied to it (one stream
+ * synchronisation); with out == NULL nothing waits for the GPU.
+ * JZ_ERR_NONFINITE if out is requested and the state holds NaN/Inf or a
+ * non-positive density or pressure. */
+int jz_rk_step(jz_solver* s, int nsteps, jz_step_stats* out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* JZ_H */

@@ -1,0 +1,414 @@
+// C ABI entry points (include/jz.h): handles, device memory, and the order of
+// the kernels in a time step (Algorithm 2 main loop).
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "jz_internal.cuh"
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return code;
+}
+
+#define JZ_CK(call)                                                                              \
+  do {                                                                                           \
+    cudaError_t e_ = (call);                                                                     \
+    if (e_ != cudaSuccess) return fail(JZ_ERR_CUDA, "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), \
+                                       __FILE__, __LINE__);                                      \
+  } while (0)
+
+const double kAlpha[5] = {0.25, 1.0 / 6.0, 0.375, 0.5, 1.0};
+
+bool is_device_ptr(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// Owner of a list of device allocations.
+struct DevMem {
+  std::vector<void*> blocks;
+  ~DevMem() { release(); }
+  void release() {
+    for (void* b : blocks) cudaFree(b);
+    blocks.clear();
+  }
+  double* alloc(size_t n, cudaError_t& err) {
+    void* p = nullptr;
+    err = cudaMalloc(&p, n * sizeof(double));
+    if (err != cudaSuccess) return nullptr;
+    blocks.push_back(p);
+    err = cudaMemset(p, 0, n * sizeof(double));
+    return static_cast<double*>(p);
+  }
+};
+
+}  // namespace
+
+struct jz_grid {
+  jz::Dims d;
+  jz::GridDev g;
+  bool metrics = false;
+  DevMem mem;
+};
+
+struct jz_solver {
+  jz_grid* grid = nullptr;
+  jz_params prm;
+  jz::Consts c;
+  cudaStream_t st = nullptr;
+  jz::State qn, qa, qb;
+  jz::Work64 w;
+  jz::Scalars* sc = nullptr;
+  jz::Inflow in;
+  double* part = nullptr;
+  double* staging = nullptr;      // [5][N], allocated on first host transfer
+  long long steps = 0;
+  long long n_adv = 0;
+  bool has_state = false;
+  DevMem mem;
+};
+
+namespace {
+
+jz::Consts make_consts(const jz_params& p) {
+  jz::Consts c;
+  c.gamma = p.gamma;
+  c.gm1 = p.gamma - 1.0;
+  c.Cp = 1.0 / c.gm1;
+  c.mu_ref = p.mach_ref / p.Re;
+  c.S_hat = p.S1_K / p.T_ref_K;
+  c.sut_num = 1.0 + c.S_hat;
+  c.k_lam = c.Cp / p.Pr;
+  c.k_sgs = c.Cp / p.Pr_sgs;
+  c.C_s = p.C_s;
+  c.kappa2 = p.kappa2;
+  c.kappa4 = p.kappa4;
+  c.sigma = p.sigma;
+  c.sigma_is_two_thirds = std::fabs(p.sigma - 2.0 / 3.0) < 1e-15 ? 1 : 0;
+  c.cfl = p.cfl;
+  c.dt_fixed = p.dt_fixed;
+  c.p_inf = 1.0 / p.gamma;
+  c.jet_mach = p.jet_mach;
+  c.theta_mom = p.theta_mom;
+  return c;
+}
+
+long long npts(const jz::Dims& d) { return (long long)d.ni * d.nj * d.nk; }
+
+int ensure_staging(jz_solver* s) {
+  if (s->staging) return JZ_OK;
+  cudaError_t e;
+  s->staging = s->mem.alloc(5 * (size_t)npts(s->grid->d), e);
+  if (!s->staging) return fail(JZ_ERR_OOM, "staging buffer: %s", cudaGetErrorString(e));
+  return JZ_OK;
+}
+
+// Copy a caller array [5][N] into the padded state q (ghosts filled).
+int load_state(jz_solver* s, const double* src, jz::State& q) {
+  const jz::Dims& d = s->grid->d;
+  const double* dev = src;
+  if (!is_device_ptr(src)) {
+    int r = ensure_staging(s);
+    if (r) return r;
+    JZ_CK(cudaMemcpyAsync(s->staging, src, 5 * sizeof(double) * npts(d), cudaMemcpyHostToDevice, s->st));
+    dev = s->staging;
+  }
+  JZ_CK(jz::pack_real(d, q.q, dev, 5, s->st));
+  JZ_CK(jz::ghost_fill(d, q.q, 5, s->st));
+  if (dev == s->staging) JZ_CK(cudaStreamSynchronize(s->st));
+  return JZ_OK;
+}
+
+int run_step(jz_solver* s) {
+  const jz::Dims& d = s->grid->d;
+  const jz::GridDev& g = s->grid->g;
+  if (s->c.dt_fixed <= 0.0) JZ_CK(jz::cfl_rate(d, s->c, g, s->qn, s->sc, s->st));
+  JZ_CK(jz::set_dt(s->c, s->sc, 0, s->st));
+  jz::State in = s->qn;
+  for (int l = 0; l < 5; ++l) {
+    jz::State out = (l % 2 == 0) ? s->qa : s->qb;
+    JZ_CK(jz::stage64(d, s->c, g, s->w, in, s->qn, out, s->sc, kAlpha[l], l, nullptr, s->st));
+    JZ_CK(jz::apply_bcs(d, s->c, g, s->in, out, s->sc, kAlpha[l], s->st));
+    JZ_CK(jz::ghost_fill(d, out.q, 5, s->st));
+    in = out;
+  }
+  // Q^{n+1} is in qa (stage 5 wrote it); it becomes Q^n.
+  jz::State t = s->qn;
+  s->qn = s->qa;
+  s->qa = t;
+  JZ_CK(jz::set_dt(s->c, s->sc, 1, s->st));
+  s->steps += 1;
+  return JZ_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* jz_last_error(void) { return g_err.c_str(); }
+
+int jz_version(void) { return 1; }
+
+int jz_create_grid(int ni, int nj, int nk, const double* xyz, const double* period, int topology,
+                   jz_grid** out) {
+  if (!out) return fail(JZ_ERR_ARG, "jz_create_grid: out is NULL");
+  *out = nullptr;
+  if (!xyz) return fail(JZ_ERR_ARG, "jz_create_grid: xyz is NULL");
+  if (topology == JZ_TOPO_PERIODIC) {
+    if (ni < 1 || nj < 1 || nk < 1) return fail(JZ_ERR_ARG, "periodic grid needs ni, nj, nk >= 1");
+    if (!period) return fail(JZ_ERR_ARG, "periodic grid needs the period vectors");
+  } else if (topology == JZ_TOPO_JET) {
+    if (ni < 4 || nj < 4 || nk < 4 || (nk % 2))
+      return fail(JZ_ERR_ARG, "jet grid needs ni >= 4, nj >= 4 and an even nk >= 4 (got %d x %d x %d)", ni, nj, nk);
+  } else {
+    return fail(JZ_ERR_ARG, "unknown topology %d", topology);
+  }
+  const jz::Dims d = jz::make_dims(ni, nj, nk, topology);
+  if (d.Np > (1LL << 40)) return fail(JZ_ERR_ARG, "grid too large");
+  jz_grid* g = new (std::nothrow) jz_grid;
+  if (!g) return fail(JZ_ERR_OOM, "host allocation failed");
+  g->d = d;
+  cudaError_t e = cudaSuccess;
+  double** slots[] = {&g->g.xyz[0], &g->g.xyz[1], &g->g.xyz[2], &g->g.S[0], &g->g.S[1], &g->g.S[2],
+                      &g->g.S[3], &g->g.S[4], &g->g.S[5], &g->g.S[6], &g->g.S[7], &g->g.S[8],
+                      &g->g.V, &g->g.invV, &g->g.Smag[0], &g->g.Smag[1], &g->g.Smag[2], &g->g.Delta};
+  for (double** sl : slots) {
+    *sl = g->mem.alloc(d.Np, e);
+    if (!*sl || e != cudaSuccess) {
+      delete g;
+      return fail(JZ_ERR_OOM, "grid arrays: %s", cudaGetErrorString(e));
+    }
+  }
+  const long long N = npts(d);
+  double* tmp = nullptr;
+  e = cudaMalloc(&tmp, 3 * sizeof(double) * N);
+  if (e != cudaSuccess) {
+    delete g;
+    return fail(JZ_ERR_OOM, "coordinate staging: %s", cudaGetErrorString(e));
+  }
+  e = cudaMemcpy(tmp, xyz, 3 * sizeof(double) * N, cudaMemcpyDefault);
+  if (e == cudaSuccess) e = jz::pad_coordinates(d, tmp, period, g->g, nullptr);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  cudaFree(tmp);
+  if (e != cudaSuccess) {
+    delete g;
+    return fail(JZ_ERR_CUDA, "jz_create_grid: %s", cudaGetErrorString(e));
+  }
+  *out = g;
+  return JZ_OK;
+}
+
+int jz_destroy_grid(jz_grid* g) {
+  if (!g) return fail(JZ_ERR_ARG, "jz_destroy_grid: NULL");
+  delete g;
+  return JZ_OK;
+}
+
+int jz_compute_metrics(jz_grid* g) {
+  if (!g) return fail(JZ_ERR_ARG, "jz_compute_metrics: NULL grid");
+  const jz::Dims& d = g->d;
+  DevMem scratch;
+  double* s9[9];
+  cudaError_t e;
+  for (int i = 0; i < 9; ++i) {
+    s9[i] = scratch.alloc(d.Np, e);
+    if (!s9[i]) return fail(JZ_ERR_OOM, "metric scratch: %s", cudaGetErrorString(e));
+  }
+  int* bad = nullptr;
+  JZ_CK(cudaMalloc(&bad, sizeof(int)));
+  scratch.blocks.push_back(bad);
+  JZ_CK(cudaMemset(bad, 0, sizeof(int)));
+  JZ_CK(jz::compute_metrics(d, g->g, s9, nullptr));
+  JZ_CK(jz::check_volume(d, g->g, bad, nullptr));
+  int nbad = 0;
+  JZ_CK(cudaMemcpy(&nbad, bad, sizeof(int), cudaMemcpyDeviceToHost));
+  if (nbad) return fail(JZ_ERR_ARG, "grid has %d advanced nodes with V <= 0", nbad);
+  g->metrics = true;
+  return JZ_OK;
+}
+
+int jz_get_metrics(const jz_grid* g, double* out) {
+  if (!g || !out) return fail(JZ_ERR_ARG, "jz_get_metrics: NULL argument");
+  if (!g->metrics) return fail(JZ_ERR_STATE, "jz_get_metrics: metrics not computed");
+  const jz::Dims& d = g->d;
+  double* M[10];
+  for (int i = 0; i < 9; ++i) M[i] = g->g.S[i];
+  M[9] = g->g.V;
+  const long long N = npts(d);
+  const bool dev = is_device_ptr(out);
+  double* dst = out;
+  double* tmp = nullptr;
+  if (!dev) {
+    JZ_CK(cudaMalloc(&tmp, 10 * sizeof(double) * N));
+    dst = tmp;
+  }
+  cudaError_t e = jz::unpack_real(d, M, dst, 10, nullptr);
+  if (e == cudaSuccess && !dev) e = cudaMemcpy(out, tmp, 10 * sizeof(double) * N, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (tmp) cudaFree(tmp);
+  if (e != cudaSuccess) return fail(JZ_ERR_CUDA, "jz_get_metrics: %s", cudaGetErrorString(e));
+  return JZ_OK;
+}
+
+int jz_create(jz_grid* g, const jz_params* p, void* stream, jz_solver** out) {
+  if (!out) return fail(JZ_ERR_ARG, "jz_create: out is NULL");
+  *out = nullptr;
+  if (!g || !p) return fail(JZ_ERR_ARG, "jz_create: NULL grid or params");
+  if (!g->metrics) return fail(JZ_ERR_STATE, "jz_create: call jz_compute_metrics first");
+  if (!(p->gamma > 1.0) || !(p->Re > 0.0) || !(p->Pr > 0.0) || !(p->Pr_sgs > 0.0) || !(p->T_ref_K > 0.0) ||
+      !(p->S1_K >= 0.0) || !(p->C_s >= 0.0) || !(p->kappa2 >= 0.0) || !(p->kappa4 >= 0.0) ||
+      !(p->sigma > 0.0 && p->sigma < 1.0) || !(p->cfl > 0.0) || !(p->dt_fixed >= 0.0))
+    return fail(JZ_ERR_ARG, "jz_create: parameter out of range");
+  if (p->precision != JZ_PREC_FP64) return fail(JZ_ERR_ARG, "jz_create: precision %d not available", p->precision);
+  jz_solver* s = new (std::nothrow) jz_solver;
+  if (!s) return fail(JZ_ERR_OOM, "host allocation failed");
+  s->grid = g;
+  s->prm = *p;
+  s->c = make_consts(*p);
+  s->st = static_cast<cudaStream_t>(stream);
+  const jz::Dims& d = g->d;
+  cudaError_t e = cudaSuccess;
+  auto A = [&](double*& dst, size_t n) {
+    if (e != cudaSuccess) return;
+    dst = s->mem.alloc(n, e);
+  };
+  for (int m = 0; m < 5; ++m) {
+    A(s->qn.q[m], d.Np);
+    A(s->qa.q[m], d.Np);
+    A(s->qb.q[m], d.Np);
+  }
+  A(s->w.u, d.Np); A(s->w.v, d.Np); A(s->w.w, d.Np); A(s->w.T, d.Np); A(s->w.p, d.Np); A(s->w.mu, d.Np);
+  for (int dir = 0; dir < 3; ++dir) {
+    A(s->w.Lam[dir], d.Np);
+    A(s->w.nu[dir], d.Np);
+    for (int m = 0; m < 5; ++m) {
+      A(s->w.H[dir][m], d.Np);
+      A(s->w.D[dir][m], d.Np);
+    }
+  }
+  double* scal = nullptr;
+  A(scal, (sizeof(jz::Scalars) + 7) / 8);
+  s->sc = reinterpret_cast<jz::Scalars*>(scal);
+  A(s->part, 8 * (size_t)jz::stat_partial_count());
+  if (d.topo == JZ_TOPO_JET) {
+    A(s->in.u0, (size_t)d.nj * d.nk);
+    A(s->in.Gf, (size_t)jz::kNF * d.nj * d.nk);
+  }
+  if (e != cudaSuccess) {
+    delete s;
+    return fail(JZ_ERR_OOM, "jz_create: device allocation failed: %s", cudaGetErrorString(e));
+  }
+  if (d.topo == JZ_TOPO_JET) {
+    e = jz::build_inflow(d, s->c, g->g, *p, s->in, s->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->st);
+    if (e != cudaSuccess) {
+      delete s;
+      return fail(JZ_ERR_CUDA, "jz_create: inflow tables: %s", cudaGetErrorString(e));
+    }
+  }
+  s->n_adv = d.topo == JZ_TOPO_JET ? (long long)(d.ni - 2) * (d.nj - 2) * d.nk : npts(d);
+  *out = s;
+  return JZ_OK;
+}
+
+int jz_destroy(jz_solver* s) {
+  if (!s) return fail(JZ_ERR_ARG, "jz_destroy: NULL");
+  cudaStreamSynchronize(s->st);
+  delete s;
+  return JZ_OK;
+}
+
+int jz_set_state(jz_solver* s, const double* q, double t) {
+  if (!s || !q) return fail(JZ_ERR_ARG, "jz_set_state: NULL argument");
+  int r = load_state(s, q, s->qn);
+  if (r) return r;
+  jz::Scalars h;
+  std::memset(&h, 0, sizeof h);
+  h.t = t;
+  JZ_CK(cudaMemcpyAsync(s->sc, &h, sizeof h, cudaMemcpyHostToDevice, s->st));
+  JZ_CK(cudaStreamSynchronize(s->st));
+  s->steps = 0;
+  s->has_state = true;
+  return JZ_OK;
+}
+
+int jz_get_state(jz_solver* s, double* q) {
+  if (!s || !q) return fail(JZ_ERR_ARG, "jz_get_state: NULL argument");
+  if (!s->has_state) return fail(JZ_ERR_STATE, "jz_get_state: no state set");
+  const jz::Dims& d = s->grid->d;
+  if (is_device_ptr(q)) {
+    JZ_CK(jz::unpack_real(d, s->qn.q, q, 5, s->st));
+    return JZ_OK;
+  }
+  int r = ensure_staging(s);
+  if (r) return r;
+  JZ_CK(jz::unpack_real(d, s->qn.q, s->staging, 5, s->st));
+  JZ_CK(cudaMemcpyAsync(q, s->staging, 5 * sizeof(double) * npts(d), cudaMemcpyDeviceToHost, s->st));
+  JZ_CK(cudaStreamSynchronize(s->st));
+  return JZ_OK;
+}
+
+int jz_residual(jz_solver* s, const double* q, double* rhs) {
+  if (!s || !q || !rhs) return fail(JZ_ERR_ARG, "jz_residual: NULL argument");
+  const jz::Dims& d = s->grid->d;
+  int r = load_state(s, q, s->qb);
+  if (r) return r;
+  const bool dev = is_device_ptr(rhs);
+  double* dst = rhs;
+  if (!dev) {
+    r = ensure_staging(s);
+    if (r) return r;
+    dst = s->staging;
+  }
+  JZ_CK(jz::stage64(d, s->c, s->grid->g, s->w, s->qb, s->qb, s->qb, s->sc, 0.0, -1, dst, s->st));
+  if (!dev) {
+    JZ_CK(cudaMemcpyAsync(rhs, dst, 5 * sizeof(double) * npts(d), cudaMemcpyDeviceToHost, s->st));
+    JZ_CK(cudaStreamSynchronize(s->st));
+  }
+  return JZ_OK;
+}
+
+int jz_rk_step(jz_solver* s, int nsteps, jz_step_stats* out) {
+  if (!s) return fail(JZ_ERR_ARG, "jz_rk_step: NULL solver");
+  if (nsteps < 0) return fail(JZ_ERR_ARG, "jz_rk_step: nsteps < 0");
+  if (!s->has_state) return fail(JZ_ERR_STATE, "jz_rk_step: no state set");
+  for (int n = 0; n < nsteps; ++n) {
+    int r = run_step(s);
+    if (r) return r;
+  }
+  if (!out) return JZ_OK;
+  const jz::Dims& d = s->grid->d;
+  JZ_CK(jz::stats_with(d, s->c, s->grid->g, s->qn, s->sc, s->part, s->st));
+  jz::Scalars h;
+  JZ_CK(cudaMemcpyAsync(&h, s->sc, sizeof h, cudaMemcpyDeviceToHost, s->st));
+  JZ_CK(cudaStreamSynchronize(s->st));
+  out->t = h.t;
+  out->dt = h.dt;
+  out->res_l2 = s->steps > 0 ? std::sqrt(h.res_sum / (double)s->n_adv) : 0.0;
+  for (int m = 0; m < 5; ++m) out->totals[m] = h.tot[m];
+  out->min_rho = h.min_rho;
+  out->min_p = h.min_p;
+  out->steps = s->steps;
+  if (h.nonfinite) return fail(JZ_ERR_NONFINITE, "state holds NaN/Inf or non-positive density/pressure");
+  return JZ_OK;
+}
+
+}  // extern "C"

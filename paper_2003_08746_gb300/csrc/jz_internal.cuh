@@ -1,0 +1,169 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstddef>
+#include <cstdint>
+#include <string>
+
+#include "../../include/jz.h"
+
+namespace jz {
+
+constexpr int kG = 2;            // ghost layers per side (two-layer ghosts)
+constexpr int kNF = JZ_N_MODES * JZ_N_FREQ;
+
+// Padded box geometry.  Real node (i, j, k), -2 <= i <= ni + 1, sits at
+// element ((k + 2) * Pj + (j + 2)) * Pi + (i + 2).  Pi is rounded up to a
+// multiple of 4 elements so that every row starts 32-byte aligned; the
+// columns past i = ni + 1 are never read by the stencil.
+struct Dims {
+  int ni, nj, nk;
+  int Pi, Pj, Pk;
+  long long Np;                  // padded elements per field
+  long long sj, sk;              // element strides of j and k
+  int topo;
+};
+
+__host__ __device__ inline long long pidx(const Dims& d, int i, int j, int k) {
+  return ((long long)(k + kG) * d.Pj + (j + kG)) * d.Pi + (i + kG);
+}
+
+inline Dims make_dims(int ni, int nj, int nk, int topo) {
+  Dims d;
+  d.ni = ni; d.nj = nj; d.nk = nk; d.topo = topo;
+  d.Pi = ((ni + 2 * kG) + 3) / 4 * 4;
+  d.Pj = nj + 2 * kG;
+  d.Pk = nk + 2 * kG;
+  d.sj = d.Pi;
+  d.sk = (long long)d.Pi * d.Pj;
+  d.Np = d.sk * d.Pk;
+  return d;
+}
+
+// Grid arrays on the device (padded, ghost-filled).
+struct GridDev {
+  double* xyz[3];
+  double* S[9];       // S^xi_{x,y,z}, S^eta_{x,y,z}, S^zeta_{x,y,z}
+  double* V;          // cell volume 1/J
+  double* invV;       // 1/V (0 where V = 0, i.e. on the jet axis)
+  double* Smag[3];    // |S^dir|
+  double* Delta;      // filter width V^(1/3)
+};
+
+// Derived constants of the non-dimensional formulation, by value.
+struct Consts {
+  double gamma, gm1, Cp;
+  double mu_ref, S_hat, sut_num;   // sut_num = 1 + S_hat
+  double k_lam, k_sgs;             // Cp/Pr, Cp/Pr_sgs
+  double C_s;
+  double kappa2, kappa4, sigma;
+  int sigma_is_two_thirds;
+  double cfl, dt_fixed;
+  double p_inf;
+  double jet_mach, theta_mom;
+};
+
+// Device scalars of a solver (one allocation).
+struct Scalars {
+  double t;          // time at the start of the current step
+  double dt;         // current time step
+  double rate_max;   // max over advanced nodes of (sum lambda)/V (as bits)
+  double res_sum;    // sum of RHS_rho^2 at stage 1
+  double tot[5];
+  double min_rho, min_p;
+  int nonfinite;
+  int pad_;
+};
+
+// FP64 stage scratch arrays (each Np elements).
+struct Work64 {
+  double* u; double* v; double* w; double* T; double* p; double* mu;
+  double* Lam[3];
+  double* H[3][5];    // transformed inviscid flux, then inviscid - viscous
+  double* nu[3];      // pressure sensor per direction
+  double* D[3][5];    // dissipation face flux at n + 1/2 per direction
+};
+
+struct State {
+  double* q[5];
+};
+
+// Inflow tables (jet): base profile u0[nk][nj] and forcing shapes
+// Gf[m*4+f][nk][nj] = g(r) cos(m theta + phi_mf), at i = 0.
+struct Inflow {
+  double* u0;
+  double* Gf;
+  double amp[kNF];
+  double psi[kNF];
+  double omega[JZ_N_FREQ];       // 2 pi St_f U_j
+};
+
+// ---- kernels' host launchers -------------------------------------------
+// metrics
+cudaError_t pad_coordinates(const Dims& d, const double* xyz_real, const double* period,
+                            GridDev& g, cudaStream_t st);
+cudaError_t compute_metrics(const Dims& d, GridDev& g, double* scratch9[9], cudaStream_t st);
+// ghost fill of nvar padded fields by the state's ghost map
+cudaError_t ghost_fill(const Dims& d, double* const* f, int nvar, cudaStream_t st);
+// copy between unpadded [nvar][N] and padded real region
+cudaError_t pack_real(const Dims& d, double* const* padded, const double* flat, int nvar,
+                      cudaStream_t st);
+cudaError_t unpack_real(const Dims& d, double* const* padded, double* flat, int nvar,
+                        cudaStream_t st);
+// FP64 stage passes
+cudaError_t stage64(const Dims& d, const Consts& c, const GridDev& g, const Work64& w,
+                    const State& qin, const State& qn, const State& qout, const Scalars* sc,
+                    double alpha, int stage, double* rhs_flat, cudaStream_t st);
+// boundary conditions (jet)
+cudaError_t apply_bcs(const Dims& d, const Consts& c, const GridDev& g, const Inflow& in,
+                      const State& q, const Scalars* sc, double alpha, cudaStream_t st);
+cudaError_t build_inflow(const Dims& d, const Consts& c, const GridDev& g, const jz_params& p,
+                         Inflow& in, cudaStream_t st);
+// reductions
+cudaError_t cfl_rate(const Dims& d, const Consts& c, const GridDev& g, const State& q,
+                     Scalars* sc, cudaStream_t st);
+cudaError_t set_dt(const Consts& c, Scalars* sc, int advance_time, cudaStream_t st);
+int stat_partial_count();
+cudaError_t stats_with(const Dims& d, const Consts& c, const GridDev& g, const State& q, Scalars* sc,
+                       double* part, cudaStream_t st);
+cudaError_t check_volume(const Dims& d, const GridDev& g, int* bad, cudaStream_t st);
+
+// ---- helpers ------------------------------------------------------------
+inline unsigned blocks_for(long long n, int tpb) { return (unsigned)((n + tpb - 1) / tpb); }
+
+// Flat thread index over a box [i0, i0+ei) x [j0, j0+ej) x [k0, k0+ek) of
+// real coordinates; returns false past the end.
+struct Box {
+  int i0, j0, k0, ei, ej, ek;
+  long long count() const { return (long long)ei * ej * ek; }
+};
+
+__device__ inline bool box_coord(const Box& b, long long t, int& i, int& j, int& k) {
+  if (t >= (long long)b.ei * b.ej * b.ek) return false;
+  i = (int)(t % b.ei);
+  long long r = t / b.ei;
+  j = (int)(r % b.ej);
+  k = (int)(r / b.ej);
+  i += b.i0; j += b.j0; k += b.k0;
+  return true;
+}
+
+// Real node whose state a padded node carries (the ghost map).
+__host__ __device__ inline void ghost_source(const Dims& d, int i, int j, int k, int& si, int& sj,
+                                             int& sk) {
+  if (d.topo == JZ_TOPO_PERIODIC) {
+    si = ((i % d.ni) + d.ni) % d.ni;
+    sj = ((j % d.nj) + d.nj) % d.nj;
+    sk = ((k % d.nk) + d.nk) % d.nk;
+    return;
+  }
+  si = i < 0 ? 0 : (i >= d.ni ? d.ni - 1 : i);
+  int kk = k;
+  if (j < 0) { sj = -j; kk = k + d.nk / 2; }
+  else if (j >= d.nj) { sj = d.nj - 1; }
+  else { sj = j; }
+  sk = ((kk % d.nk) + d.nk) % d.nk;
+}
+
+}  // namespace jz

@@ -1,0 +1,227 @@
+// FP64 form of one Runge-Kutta stage (Algorithm 2, lines Calc(Inv. Flux) to
+// Update(Cons., alpha_l)), as four passes over the padded grid.
+//
+// The FP64 pipe of a GB300 runs at ~1/70 of its FP32 rate, so this form is
+// bound by FP64 arithmetic, not by HBM.  Each pass therefore computes every
+// nodal or face quantity exactly once and hands it to the next pass through
+// HBM (no halo recomputation); the extra traffic costs far less time than
+// the FP64 operations it saves.
+//
+//  A  nodal     (all padded nodes): primitives u, v, w, p, T; Sutherland mu;
+//               spectral radii and their anisotropic scaling Lambda_dir;
+//               transformed inviscid fluxes E^dir = S^dir_j E_j.
+//  B  viscous   (nodes within one layer of the real region): Cartesian
+//               gradients by the chain rule, strain rate, Smagorinsky eddy
+//               viscosity, stresses and heat flux; H^dir = E^dir - S^dir_j F_j
+//               (in place over E^dir); pressure sensor nu_dir.
+//  C  faces     Turkel-Vatsa dissipation flux d_{n+1/2} for each direction.
+//  D  update    V RHS = sum_dir [delta_dir H^dir - (d_{n+1/2} - d_{n-1/2})],
+//               Q^(l) = Q^n - alpha_l dt RHS on the advanced nodes.
+#include "jz_internal.cuh"
+
+namespace jz {
+namespace {
+
+constexpr int kTPB = 256;
+
+__device__ __forceinline__ bool advanced(const Dims& d, int i, int j) {
+  return d.topo != JZ_TOPO_JET || (i >= 1 && i <= d.ni - 2 && j >= 1 && j <= d.nj - 2);
+}
+
+// Anisotropic spectral radius lambda_d + lambda_d^(1-sigma) (lambda_e^sigma + lambda_f^sigma).
+__device__ __forceinline__ void aniso(const Consts& c, const double lam[3], double Lam[3]) {
+  double lo[3], hi[3];
+  if (c.sigma_is_two_thirds) {
+    for (int d = 0; d < 3; ++d) {
+      const double t = cbrt(lam[d]);
+      lo[d] = t;
+      hi[d] = t * t;
+    }
+  } else {
+    for (int d = 0; d < 3; ++d) {
+      lo[d] = lam[d] > 0.0 ? pow(lam[d], 1.0 - c.sigma) : 0.0;
+      hi[d] = lam[d] > 0.0 ? pow(lam[d], c.sigma) : 0.0;
+    }
+  }
+  Lam[0] = lam[0] + lo[0] * (hi[1] + hi[2]);
+  Lam[1] = lam[1] + lo[1] * (hi[0] + hi[2]);
+  Lam[2] = lam[2] + lo[2] * (hi[0] + hi[1]);
+}
+
+__global__ void __launch_bounds__(kTPB) k_nodal(Dims d, Consts c, GridDev g, Work64 w, State q) {
+  Box b{-kG, -kG, -kG, d.ni + 2 * kG, d.nj + 2 * kG, d.nk + 2 * kG};
+  int i, j, k;
+  if (!box_coord(b, blockIdx.x * (long long)blockDim.x + threadIdx.x, i, j, k)) return;
+  const long long p = pidx(d, i, j, k);
+  const double rho = q.q[0][p], m1 = q.q[1][p], m2 = q.q[2][p], m3 = q.q[3][p], e = q.q[4][p];
+  const double u = m1 / rho, v = m2 / rho, ww = m3 / rho;
+  const double pr = c.gm1 * (e - 0.5 * (m1 * u + m2 * v + m3 * ww));
+  const double T = c.gamma * pr / rho;
+  const double a = sqrt(T);
+  // Sutherland, eq. (sutherland), with T_inf = 1
+  const double mu = c.mu_ref * (T * a) * c.sut_num / (T + c.S_hat);
+  w.u[p] = u; w.v[p] = v; w.w[p] = ww; w.T[p] = T; w.p[p] = pr; w.mu[p] = mu;
+  double lam[3];
+  for (int dir = 0; dir < 3; ++dir) {
+    const double sx = g.S[3 * dir][p], sy = g.S[3 * dir + 1][p], sz = g.S[3 * dir + 2][p];
+    const double U = sx * u + sy * v + sz * ww;
+    lam[dir] = fabs(U) + a * g.Smag[dir][p];
+    w.H[dir][0][p] = rho * U;
+    w.H[dir][1][p] = m1 * U + pr * sx;
+    w.H[dir][2][p] = m2 * U + pr * sy;
+    w.H[dir][3][p] = m3 * U + pr * sz;
+    w.H[dir][4][p] = (e + pr) * U;
+  }
+  double Lam[3];
+  aniso(c, lam, Lam);
+  w.Lam[0][p] = Lam[0]; w.Lam[1][p] = Lam[1]; w.Lam[2][p] = Lam[2];
+}
+
+__global__ void __launch_bounds__(kTPB) k_viscous(Dims d, Consts c, GridDev g, Work64 w, State q) {
+  Box b{-1, -1, -1, d.ni + 2, d.nj + 2, d.nk + 2};
+  int i, j, k;
+  if (!box_coord(b, blockIdx.x * (long long)blockDim.x + threadIdx.x, i, j, k)) return;
+  const long long p = pidx(d, i, j, k);
+  const long long s[3] = {1, d.sj, d.sk};
+  const double* f[4] = {w.u, w.v, w.w, w.T};
+  double S[3][3];
+  for (int dir = 0; dir < 3; ++dir)
+    for (int cc = 0; cc < 3; ++cc) S[dir][cc] = g.S[3 * dir + cc][p];
+  const double iV = g.invV[p];
+  // L[n][j] = d f_n / d x_j = (1/V) sum_dir S^dir_j delta_dir f_n
+  double L[4][3];
+  for (int n = 0; n < 4; ++n) {
+    double dd[3];
+    for (int dir = 0; dir < 3; ++dir) dd[dir] = 0.5 * (f[n][p + s[dir]] - f[n][p - s[dir]]);
+    for (int jj = 0; jj < 3; ++jj) L[n][jj] = iV * (S[0][jj] * dd[0] + S[1][jj] * dd[1] + S[2][jj] * dd[2]);
+  }
+  double Sij[3][3];
+  for (int a = 0; a < 3; ++a)
+    for (int bb = 0; bb < 3; ++bb) Sij[a][bb] = 0.5 * (L[a][bb] + L[bb][a]);
+  const double div = Sij[0][0] + Sij[1][1] + Sij[2][2];
+  double SS = 0.0;
+  for (int a = 0; a < 3; ++a)
+    for (int bb = 0; bb < 3; ++bb) SS = SS + Sij[a][bb] * Sij[a][bb];
+  const double Smod = sqrt(2.0 * SS);
+  const double mu = w.mu[p];
+  const double csd = c.C_s * g.Delta[p];
+  const double mu_sgs = q.q[0][p] * (csd * csd) * Smod;
+  const double mu_eff = mu + mu_sgs;
+  const double k_eff = mu * c.k_lam + mu_sgs * c.k_sgs;
+  double tau[3][3];
+  for (int a = 0; a < 3; ++a)
+    for (int bb = 0; bb < 3; ++bb) tau[a][bb] = 2.0 * mu_eff * (Sij[a][bb] - (a == bb ? div / 3.0 : 0.0));
+  const double vel[3] = {w.u[p], w.v[p], w.w[p]};
+  // Cartesian viscous flux in direction jj: [tau_1j, tau_2j, tau_3j, u_i tau_ij + k dT/dx_j]
+  double F[3][4];
+  for (int jj = 0; jj < 3; ++jj) {
+    F[jj][0] = tau[0][jj];
+    F[jj][1] = tau[1][jj];
+    F[jj][2] = tau[2][jj];
+    F[jj][3] = vel[0] * tau[0][jj] + vel[1] * tau[1][jj] + vel[2] * tau[2][jj] + k_eff * L[3][jj];
+  }
+  for (int dir = 0; dir < 3; ++dir)
+    for (int m = 0; m < 4; ++m) {
+      const double fv = S[dir][0] * F[0][m] + S[dir][1] * F[1][m] + S[dir][2] * F[2][m];
+      w.H[dir][m + 1][p] = w.H[dir][m + 1][p] - fv;
+    }
+  // pressure sensor along each direction
+  const double pc = w.p[p];
+  for (int dir = 0; dir < 3; ++dir) {
+    const double pp = w.p[p + s[dir]], pm = w.p[p - s[dir]];
+    w.nu[dir][p] = fabs(pp - 2.0 * pc + pm) / (pp + 2.0 * pc + pm);
+  }
+}
+
+__global__ void __launch_bounds__(kTPB) k_faces(Dims d, Consts c, Work64 w, State q) {
+  Box b{-1, -1, -1, d.ni + 1, d.nj + 1, d.nk + 1};
+  int i, j, k;
+  if (!box_coord(b, blockIdx.x * (long long)blockDim.x + threadIdx.x, i, j, k)) return;
+  const long long p = pidx(d, i, j, k);
+  const long long s[3] = {1, d.sj, d.sk};
+  for (int dir = 0; dir < 3; ++dir) {
+    const long long sd = s[dir];
+    const double nu0 = w.nu[dir][p], nu1 = w.nu[dir][p + sd];
+    const double eps2 = c.kappa2 * (nu0 >= nu1 ? nu0 : nu1);
+    const double k4 = c.kappa4 - eps2;
+    const double eps4 = k4 > 0.0 ? k4 : 0.0;
+    const double Lf = 0.5 * (w.Lam[dir][p] + w.Lam[dir][p + sd]);
+    for (int m = 0; m < 5; ++m) {
+      const double* Q = q.q[m];
+      const double q0 = Q[p], q1 = Q[p + sd], q2 = Q[p + 2 * sd], qm = Q[p - sd];
+      const double d1 = q1 - q0;
+      const double d3 = q2 - 3.0 * q1 + 3.0 * q0 - qm;
+      w.D[dir][m][p] = Lf * (eps2 * d1 - eps4 * d3);
+    }
+  }
+}
+
+// mode 0: stage update; mode 1: write RHS to rhs_flat (unpadded [5][N]).
+template <int MODE>
+__global__ void __launch_bounds__(kTPB) k_update(Dims d, GridDev g, Work64 w, State qin, State qn, State qout,
+                                                 const Scalars* sc, double alpha, int want_res,
+                                                 double* rhs_flat, double* res_sum) {
+  Box b{0, 0, 0, d.ni, d.nj, d.nk};
+  int i, j, k;
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  double r2 = 0.0;
+  if (box_coord(b, t, i, j, k)) {
+    const long long p = pidx(d, i, j, k);
+    const long long s[3] = {1, d.sj, d.sk};
+    const bool adv = advanced(d, i, j);
+    const double iV = g.invV[p];
+    double R[5];
+    for (int m = 0; m < 5; ++m) {
+      double acc = 0.0;
+      for (int dir = 0; dir < 3; ++dir) {
+        const double* H = w.H[dir][m];
+        const double* D = w.D[dir][m];
+        acc = acc + 0.5 * (H[p + s[dir]] - H[p - s[dir]]) - (D[p] - D[p - s[dir]]);
+      }
+      R[m] = acc * iV;
+    }
+    if (MODE == 0) {
+      const double adt = alpha * sc->dt;
+      for (int m = 0; m < 5; ++m) qout.q[m][p] = adv ? qn.q[m][p] - adt * R[m] : qin.q[m][p];
+    } else {
+      const long long N = (long long)d.ni * d.nj * d.nk;
+      for (int m = 0; m < 5; ++m) rhs_flat[m * N + t] = adv ? R[m] : 0.0;
+    }
+    if (adv) r2 = R[0] * R[0];
+  }
+  if (want_res) {
+    // block sum of RHS_rho^2 -> one atomic per block
+    __shared__ double red[kTPB / 32];
+    for (int o = 16; o > 0; o >>= 1) r2 += __shfl_xor_sync(0xffffffffu, r2, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = r2;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+      double x = threadIdx.x < kTPB / 32 ? red[threadIdx.x] : 0.0;
+      for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+      if (threadIdx.x == 0) atomicAdd(res_sum, x);
+    }
+  }
+}
+
+}  // namespace
+
+cudaError_t stage64(const Dims& d, const Consts& c, const GridDev& g, const Work64& w, const State& qin,
+                    const State& qn, const State& qout, const Scalars* sc, double alpha, int stage,
+                    double* rhs_flat, cudaStream_t st) {
+  const long long n0 = (long long)(d.ni + 2 * kG) * (d.nj + 2 * kG) * (d.nk + 2 * kG);
+  const long long n1 = (long long)(d.ni + 2) * (d.nj + 2) * (d.nk + 2);
+  const long long nf = (long long)(d.ni + 1) * (d.nj + 1) * (d.nk + 1);
+  const long long nr = (long long)d.ni * d.nj * d.nk;
+  k_nodal<<<blocks_for(n0, kTPB), kTPB, 0, st>>>(d, c, g, w, qin);
+  k_viscous<<<blocks_for(n1, kTPB), kTPB, 0, st>>>(d, c, g, w, qin);
+  k_faces<<<blocks_for(nf, kTPB), kTPB, 0, st>>>(d, c, w, qin);
+  double* res_sum = const_cast<double*>(&sc->res_sum);
+  if (rhs_flat)
+    k_update<1><<<blocks_for(nr, kTPB), kTPB, 0, st>>>(d, g, w, qin, qn, qout, sc, alpha, 0, rhs_flat, res_sum);
+  else
+    k_update<0><<<blocks_for(nr, kTPB), kTPB, 0, st>>>(d, g, w, qin, qn, qout, sc, alpha, stage == 0, nullptr,
+                                                       res_sum);
+  return cudaGetLastError();
+}
+
+}  // namespace jz

@@ -1,0 +1,247 @@
+"""Thin ctypes binding of the C ABI in include/jz.h (argument marshalling only).
+
+Every step of the solver runs in the CUDA library ``_build/libjz.so``; this
+module only converts Python/NumPy/torch arguments to pointers and status
+codes to exceptions.  There is no CPU fallback: if the library is missing,
+loading fails loudly.
+
+Functions keep the C names (``jz_create_grid``, ``jz_rk_step``, ...); the
+``Grid`` and ``Solver`` classes own the handles.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libjz.so")
+
+JZ_OK, JZ_ERR_ARG, JZ_ERR_CUDA, JZ_ERR_OOM, JZ_ERR_NONFINITE, JZ_ERR_STATE = 0, -1, -2, -3, -4, -5
+JZ_TOPO_PERIODIC, JZ_TOPO_JET = 1, 2
+JZ_PREC_FP64, JZ_PREC_FP32FLUX = 0, 1
+N_MODES, N_FREQ = 8, 4
+
+# Entry points declared in include/jz.h (checked by the tests).
+EXPORTS = ("jz_last_error", "jz_version", "jz_create_grid", "jz_destroy_grid", "jz_compute_metrics",
+           "jz_get_metrics", "jz_create", "jz_destroy", "jz_set_state", "jz_get_state", "jz_residual",
+           "jz_rk_step")
+
+
+class JzError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"jz error {code}: {msg}")
+        self.code = code
+
+
+class jz_params(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_double) for n in (
+        "gamma", "Pr", "Pr_sgs", "Re", "mach_ref", "T_ref_K", "S1_K", "C_s", "kappa2", "kappa4",
+        "sigma", "cfl", "dt_fixed", "jet_mach", "theta_mom")] + [
+        ("forcing_amp", ctypes.c_double * (N_MODES * N_FREQ)),
+        ("forcing_phi", ctypes.c_double * (N_MODES * N_FREQ)),
+        ("forcing_psi", ctypes.c_double * (N_MODES * N_FREQ)),
+        ("strouhal", ctypes.c_double * N_FREQ),
+        ("precision", ctypes.c_int)]
+
+
+class jz_step_stats(ctypes.Structure):
+    _fields_ = [("t", ctypes.c_double), ("dt", ctypes.c_double), ("res_l2", ctypes.c_double),
+                ("totals", ctypes.c_double * 5), ("min_rho", ctypes.c_double), ("min_p", ctypes.c_double),
+                ("steps", ctypes.c_longlong)]
+
+
+_lib = None
+
+
+def load(path: str | None = None) -> ctypes.CDLL:
+    """Load libjz.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or LIB_PATH
+    if not os.path.exists(path):
+        raise ImportError(f"CUDA library {path} is missing: build it with paper_2003_08746_gb300.build.build()")
+    lib = ctypes.CDLL(path)
+    vp, i, d = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+    sig = {
+        "jz_last_error": ([], ctypes.c_char_p),
+        "jz_version": ([], i),
+        "jz_create_grid": ([i, i, i, vp, vp, i, ctypes.POINTER(vp)], i),
+        "jz_destroy_grid": ([vp], i),
+        "jz_compute_metrics": ([vp], i),
+        "jz_get_metrics": ([vp, vp], i),
+        "jz_create": ([vp, ctypes.POINTER(jz_params), vp, ctypes.POINTER(vp)], i),
+        "jz_destroy": ([vp], i),
+        "jz_set_state": ([vp, vp, d], i),
+        "jz_get_state": ([vp, vp], i),
+        "jz_residual": ([vp, vp, vp], i),
+        "jz_rk_step": ([vp, i, ctypes.POINTER(jz_step_stats)], i),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes, fn.restype = args, res
+    _lib = lib
+    return lib
+
+
+def _check(code: int) -> None:
+    if code != JZ_OK:
+        raise JzError(code, load().jz_last_error().decode())
+
+
+def _ptr(x):
+    """Data pointer of a C-contiguous float64 NumPy array or torch tensor (CPU or CUDA)."""
+    if isinstance(x, np.ndarray):
+        if x.dtype != np.float64 or not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("expected a C-contiguous float64 array")
+        return ctypes.c_void_p(x.ctypes.data)
+    import torch
+    if isinstance(x, torch.Tensor):
+        if x.dtype != torch.float64 or not x.is_contiguous():
+            raise ValueError("expected a contiguous float64 tensor")
+        return ctypes.c_void_p(x.data_ptr())
+    raise TypeError(f"unsupported array type {type(x)}")
+
+
+# --- C names ---------------------------------------------------------------
+def jz_version() -> int:
+    return load().jz_version()
+
+
+def jz_create_grid(ni, nj, nk, xyz, period, topology):
+    h = ctypes.c_void_p()
+    per = None if period is None else np.ascontiguousarray(period, dtype=np.float64).reshape(9)
+    _check(load().jz_create_grid(ni, nj, nk, _ptr(xyz), None if per is None else _ptr(per), topology,
+                                 ctypes.byref(h)))
+    return h
+
+
+def jz_destroy_grid(h):
+    _check(load().jz_destroy_grid(h))
+
+
+def jz_compute_metrics(h):
+    _check(load().jz_compute_metrics(h))
+
+
+def jz_get_metrics(h, out):
+    _check(load().jz_get_metrics(h, _ptr(out)))
+
+
+def make_params(prm, precision: int = JZ_PREC_FP64) -> jz_params:
+    """jz_params from a workloads.FlowParams-like object (plain values)."""
+    p = jz_params()
+    for name in ("gamma", "Pr", "Pr_sgs", "Re", "mach_ref", "T_ref_K", "S1_K", "C_s", "kappa2", "kappa4",
+                 "sigma", "cfl", "dt_fixed", "jet_mach", "theta_mom"):
+        setattr(p, name, float(getattr(prm, name)))
+    for name in ("forcing_amp", "forcing_phi", "forcing_psi"):
+        v = getattr(prm, name, None)
+        arr = np.zeros(N_MODES * N_FREQ) if v is None else np.asarray(v, dtype=np.float64).reshape(-1)
+        getattr(p, name)[:] = list(arr)
+    p.strouhal[:] = [float(s) for s in prm.strouhal]
+    p.precision = int(precision)
+    return p
+
+
+def jz_create(grid_h, params: jz_params, stream=None):
+    h = ctypes.c_void_p()
+    st = ctypes.c_void_p(0 if stream is None else int(stream))
+    _check(load().jz_create(grid_h, ctypes.byref(params), st, ctypes.byref(h)))
+    return h
+
+
+def jz_destroy(h):
+    _check(load().jz_destroy(h))
+
+
+def jz_set_state(h, q, t: float = 0.0):
+    _check(load().jz_set_state(h, _ptr(q), float(t)))
+
+
+def jz_get_state(h, q):
+    _check(load().jz_get_state(h, _ptr(q)))
+
+
+def jz_residual(h, q, rhs):
+    _check(load().jz_residual(h, _ptr(q), _ptr(rhs)))
+
+
+def jz_rk_step(h, nsteps: int, want_stats: bool = True):
+    st = jz_step_stats() if want_stats else None
+    _check(load().jz_rk_step(h, int(nsteps), ctypes.byref(st) if st is not None else None))
+    return st
+
+
+# --- owners ----------------------------------------------------------------
+class Grid:
+    """Owner of a jz_grid handle; metrics are computed on construction."""
+
+    def __init__(self, ni, nj, nk, xyz, topology, period=None):
+        self.ni, self.nj, self.nk, self.topology = int(ni), int(nj), int(nk), int(topology)
+        self._xyz = xyz
+        self.h = jz_create_grid(self.ni, self.nj, self.nk, xyz, period, self.topology)
+        jz_compute_metrics(self.h)
+
+    @classmethod
+    def from_workload(cls, g):
+        return cls(g.ni, g.nj, g.nk, g.xyz, g.topology, g.period)
+
+    @property
+    def npts(self):
+        return self.ni * self.nj * self.nk
+
+    def metrics(self):
+        out = np.empty((10, self.nk, self.nj, self.ni))
+        jz_get_metrics(self.h, out)
+        return out
+
+    def close(self):
+        if self.h:
+            jz_destroy_grid(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Solver:
+    """Owner of a jz_solver handle on a Grid."""
+
+    def __init__(self, grid: Grid, prm, precision: int = JZ_PREC_FP64, stream=None):
+        self.grid = grid
+        self.params = make_params(prm, precision)
+        self.h = jz_create(grid.h, self.params, stream)
+
+    def set_state(self, q, t: float = 0.0):
+        jz_set_state(self.h, q, t)
+
+    def get_state(self, out=None):
+        if out is None:
+            out = np.empty((5, self.grid.nk, self.grid.nj, self.grid.ni))
+        jz_get_state(self.h, out)
+        return out
+
+    def residual(self, q, out=None):
+        if out is None:
+            out = np.empty((5, self.grid.nk, self.grid.nj, self.grid.ni))
+        jz_residual(self.h, q, out)
+        return out
+
+    def step(self, nsteps: int = 1, stats: bool = True):
+        return jz_rk_step(self.h, nsteps, stats)
+
+    def close(self):
+        if self.h:
+            jz_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,158 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle, FP64 form.
+
+Element-wise comparison on the same seeded inputs.  Bar: relative L2 error of
+every field <= 1e-12 (and max-abs error <= 1e-11 of the field's scale).
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import jz_oracle as O
+from paper_2003_08746_gb300 import workloads as W
+from parity import field_errors, oracle_grid
+
+pytestmark = pytest.mark.gpu
+
+TOL_L2 = 1e-12
+TOL_MAX = 1e-11
+
+
+@pytest.fixture(scope="module")
+def jz():
+    from paper_2003_08746_gb300 import build, jz as J
+    build.build()
+    J.load()
+    assert torch.cuda.is_available()
+    return J
+
+
+def _case(name):
+    if name == "box_ragged":
+        g = W.box_grid(37, 29, 19, h=0.17)
+        return g, W.random_state(g, seed=21, amp=0.05), W.box_params()
+    if name == "box32x24x16":
+        return W.make_workload("box32x24x16")
+    if name == "wavy":
+        g = W.wavy_periodic_grid(40, 28, 20, amp=0.08)
+        return g, W.smooth_state(g, seed=3, amp=0.1), W.box_params(Re=200.0)
+    if name == "jet_ragged":
+        g = W.jet_grid(70, 34, 16)
+        # parallel jet plus a small seeded perturbation of every conserved variable
+        noise = W.random_state(g, seed=5, amp=2e-3, base_u=(0, 0, 0)) - W.random_state(g, seed=5, amp=0.0,
+                                                                                      base_u=(0, 0, 0))
+        return g, W.jet_state(g) + noise, W.jet_params(seed=2)
+    if name == "jet64x32x16":
+        return W.make_workload("jet64x32x16")
+    raise KeyError(name)
+
+
+CASES = ["box_ragged", "wavy", "jet_ragged"]
+
+
+@pytest.mark.parametrize("name", CASES)
+def test_metrics_parity(jz, name):
+    g, _, _ = _case(name)
+    grid = jz.Grid.from_workload(g)
+    got = grid.metrics()
+    ref = oracle_grid(g).metrics_real.numpy()
+    scale = np.abs(ref[:9]).max()
+    assert np.abs(got[:9] - ref[:9]).max() <= 1e-13 * scale
+    assert np.abs(got[9] - ref[9]).max() <= 1e-13 * np.abs(ref[9]).max()
+
+
+@pytest.mark.parametrize("name", CASES)
+@pytest.mark.parametrize("where", ["host", "device"])
+def test_residual_parity(jz, name, where):
+    g, q, prm = _case(name)
+    grid = jz.Grid.from_workload(g)
+    s = jz.Solver(grid, prm)
+    if where == "host":
+        got = s.residual(q)
+    else:
+        qd = torch.from_numpy(q).cuda()
+        out = torch.empty_like(qd)
+        s.residual(qd, out)
+        got = out.cpu().numpy()
+    ref = O.residual(oracle_grid(g), torch.from_numpy(q), O.Consts(prm)).numpy()
+    e2, em = field_errors(got, ref)
+    assert e2.max() <= TOL_L2, e2
+    assert em.max() <= TOL_MAX, em
+
+
+@pytest.mark.parametrize("name,nsteps", [("box32x24x16", 10), ("box_ragged", 3), ("wavy", 3),
+                                         ("jet_ragged", 4), ("jet64x32x16", 20)])
+def test_rk_steps_parity(jz, name, nsteps):
+    g, q, prm = _case(name)
+    grid = jz.Grid.from_workload(g)
+    s = jz.Solver(grid, prm)
+    s.set_state(q, 0.25)
+    st = s.step(nsteps)
+    got = s.get_state()
+    og, oc = oracle_grid(g), O.Consts(prm)
+    ref, t, dts, R1 = O.run(og, torch.from_numpy(q), oc, nsteps, t0=0.25)
+    e2, em = field_errors(got, ref.numpy())
+    assert e2.max() <= TOL_L2, e2
+    assert em.max() <= TOL_MAX, em
+    assert abs(st.t - t.item()) <= 1e-13 * abs(t.item())
+    assert abs(st.dt - dts[-1].item()) <= 1e-13 * dts[-1].item()
+    assert st.steps == nsteps
+    res = O.residual_l2(og, R1).item()
+    assert abs(st.res_l2 - res) <= 1e-11 * res
+    tot = O.totals(og, ref).numpy()
+    scale = np.abs(ref.numpy() * og.metrics_real[9].numpy()).reshape(5, -1).sum(1)
+    assert np.all(np.abs(np.array(st.totals) - tot) <= 1e-13 * scale)
+
+
+def test_box_conservation_on_gpu(jz):
+    """Config 1 box: totals of Q V constant to round-off over 10 steps on the GPU path."""
+    g, q, prm = W.make_workload("box32x24x16")
+    grid = jz.Grid.from_workload(g)
+    s = jz.Solver(grid, prm)
+    s.set_state(q)
+    st0 = s.step(0)
+    st = s.step(10)
+    scale = np.abs(q * grid.metrics()[9]).reshape(5, -1).sum(1)
+    drift = np.abs(np.array(st.totals) - np.array(st0.totals)) / scale
+    assert drift.max() < 1e-13
+
+
+def test_fixed_dt_and_time(jz):
+    g, q, prm = _case("jet_ragged")
+    prm.dt_fixed = 1e-3
+    grid = jz.Grid.from_workload(g)
+    s = jz.Solver(grid, prm)
+    s.set_state(q, 1.5)
+    st = s.step(3)
+    assert st.dt == 1e-3 and abs(st.t - 1.503) < 1e-14
+    ref, _, _, _ = O.run(oracle_grid(g), torch.from_numpy(q), O.Consts(prm), 3, t0=1.5)
+    e2, _ = field_errors(s.get_state(), ref.numpy())
+    assert e2.max() <= TOL_L2
+
+
+def test_nonfinite_state_is_reported(jz):
+    """A NaN in the state is reported as JZ_ERR_NONFINITE by the statistics (host-side check)."""
+    g, q, prm = _case("box_ragged")
+    q = q.copy()
+    q[0, 3, 4, 5] = np.nan
+    grid = jz.Grid.from_workload(g)
+    s = jz.Solver(grid, prm)
+    s.set_state(q)
+    with pytest.raises(jz.JzError) as ei:
+        s.step(0)
+    assert ei.value.code == jz.JZ_ERR_NONFINITE
+
+
+def test_jet_full_size_one_step(jz):
+    """Jet 256 x 128 x 64 (2.1M points): one full RK step against the oracle."""
+    g, q, prm = W.make_workload("jet256x128x64")
+    grid = jz.Grid.from_workload(g)
+    s = jz.Solver(grid, prm)
+    s.set_state(torch.from_numpy(q).cuda())
+    s.step(1)
+    got = s.get_state()
+    ref, _, _, _ = O.run(oracle_grid(g), torch.from_numpy(q), O.Consts(prm), 1)
+    e2, em = field_errors(got, ref.numpy())
+    assert e2.max() <= TOL_L2, e2
+    assert em.max() <= TOL_MAX, em

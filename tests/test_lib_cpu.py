@@ -1,0 +1,80 @@
+"""Host-side checks of the C ABI library (no GPU needed): it builds for sm_103a,
+loads, and exports every entry point that include/jz.h declares."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_functions():
+    names = []
+    for fn in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if fn.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", fn)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names += re.findall(r"^\s*(?:const\s+)?\w+\s*\*?\s*(jz_\w+)\s*\(", src, flags=re.M)
+    return names
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2003_08746_gb300 import build
+    path = build.build()
+    return ctypes.CDLL(path)
+
+
+def test_header_declares_the_boundary():
+    names = _declared_functions()
+    for required in ("jz_create_grid", "jz_compute_metrics", "jz_set_state", "jz_rk_step", "jz_residual",
+                     "jz_get_metrics", "jz_create", "jz_destroy"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    missing = [n for n in _declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_binding_matches_header(lib):
+    from paper_2003_08746_gb300 import jz
+    assert set(jz.EXPORTS) <= set(_declared_functions())
+    assert set(_declared_functions()) <= set(jz.EXPORTS) | {"jz_adjoint_step"}
+
+
+def test_version_and_error_without_gpu(lib):
+    lib.jz_version.restype = ctypes.c_int
+    assert lib.jz_version() >= 1
+    lib.jz_last_error.restype = ctypes.c_char_p
+    assert lib.jz_last_error() is not None
+
+
+def test_argument_errors_do_not_need_a_gpu(lib):
+    """Bad sizes and NULL pointers are rejected before any CUDA call."""
+    vp = ctypes.c_void_p
+    lib.jz_create_grid.argtypes = [ctypes.c_int] * 3 + [vp, vp, ctypes.c_int, ctypes.POINTER(vp)]
+    lib.jz_create_grid.restype = ctypes.c_int
+    lib.jz_last_error.restype = ctypes.c_char_p
+    h = vp()
+    buf = (ctypes.c_double * 48)()
+    assert lib.jz_create_grid(4, 4, 3, ctypes.cast(buf, vp), None, 2, ctypes.byref(h)) == -1   # odd nk
+    assert b"even" in lib.jz_last_error()
+    assert lib.jz_create_grid(4, 4, 4, None, None, 2, ctypes.byref(h)) == -1
+    assert lib.jz_create_grid(4, 4, 4, ctypes.cast(buf, vp), None, 1, ctypes.byref(h)) == -1   # no period
+    assert lib.jz_create_grid(4, 4, 4, ctypes.cast(buf, vp), None, 7, ctypes.byref(h)) == -1
+    lib.jz_rk_step.argtypes = [vp, ctypes.c_int, vp]
+    assert lib.jz_rk_step(None, 1, None) == -1
+    lib.jz_destroy.argtypes = [vp]
+    assert lib.jz_destroy(None) == -1
+
+
+def test_product_path_has_no_oracle_import():
+    """The library package never imports the oracle (no CPU fallback)."""
+    pkg = os.path.join(ROOT, "paper_2003_08746_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for fn in files:
+            if fn.endswith((".py", ".cu", ".cuh", ".h")):
+                src = open(os.path.join(dirpath, fn)).read()
+                assert "from oracle" not in src and "import oracle" not in src
