@@ -1,0 +1,266 @@
+"""Throughput benchmark of the stage-residual / RK-update hot path on GB300.
+
+One bench step = one explicit 5-stage Runge-Kutta time step (all stages,
+boundary conditions, ghost fills and the CFL reduction) of the jet workload
+1000 (axial) x 400 (radial) x 500 (azimuthal) = 2.0e8 points (1.0e9 degrees
+of freedom), the largest single-GPU configuration of the paper-shaped runs.
+Metric: grid-point-stage updates per second (points x 5 stages x steps / s).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank runs an independent replica of the
+workload on its own GPU (no domain decomposition); value = all ranks' point
+stages / max-over-ranks time.  The reference arm (--impl reference) times the
+CPU oracle on the host cores on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "jet1000x400x500"
+SAMPLE = (400, 160, 200)         # CPU sample: same jet recipe, 1/15.6 of the points
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+# FP64 peak from unit counts and clock: 152 SMs x 4 FP64 flop/clk/SM (2 DFMA) x 2.07 GHz
+FP64_PEAK_TFLOPS = 152 * 4 * 2.07e9 / 1e12
+
+# Algorithmic FP64 flops per point of each FP64 stage kernel (add/sub/mul = 1,
+# fused multiply-add = 2, divide/sqrt/cbrt = 1), counted from the operations
+# the method needs per node (each quantity once).
+FLOPS_PER_POINT = {"nodal": 82, "viscous": 272, "faces": 168, "update": 91}
+# DRAM bytes per node of a kernel launch from an ncu capture (dram__bytes_read.sum +
+# dram__bytes_write.sum / nodes), scaled to the full launch by its node count;
+# profiles/k_viscous_fp64_jet256x128x64.md.
+TRAFFIC_PER_NODE = {"viscous": 347.0}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi SM clock / throttle-reason samples while the timed region runs."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.samples = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 8:
+                self.samples.append(parts)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm = [float(s[0]) for s in self.samples if s[0].replace(".", "").isdigit()]
+        smax = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for s in self.samples for i in range(4) if s[4 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": reasons, "samples": len(self.samples)}
+
+
+def oracle_sample_rate(steps: int, shape=SAMPLE):
+    """Oracle throughput (point-stages/s) on a bounded sample of the jet workload."""
+    import torch
+    from oracle import jz_oracle as O
+    from paper_2003_08746_gb300 import workloads as W
+    g = W.jet_grid(*shape, axial_stretch=True)
+    prm = W.jet_params(seed=2)
+    q = torch.from_numpy(W.jet_state(g))
+    grid, c = O.Grid(g.ni, g.nj, g.nk, g.xyz, g.topology, g.period), O.Consts(prm)
+    t0 = time.perf_counter()
+    O.run(grid, q, c, steps)
+    dt = time.perf_counter() - t0
+    return g.npts * 5 * steps / dt, dt, torch.get_num_threads()
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    warm = max(args.warmup, 0)
+    if warm:
+        oracle_sample_rate(1)
+    rate, secs, threads = oracle_sample_rate(args.steps)
+    value = rate / 1e9
+    sample = f"jet {SAMPLE[0]}x{SAMPLE[1]}x{SAMPLE[2]} (same recipe as {WORKLOAD}), {args.steps} RK steps"
+    line = {"impl": "reference", "metric": "Gpoint-stage updates/s", "value": value, "unit": "Gpoint-stage/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": secs * 1e3 / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample": sample, "precision": "fp64"},
+            "cpu_baseline": {"value": value, "unit": "Gpoint-stage/s", "cores": threads, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "Gpoint-stage/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import torch.distributed as dist
+    from paper_2003_08746_gb300 import build, jz
+    from paper_2003_08746_gb300 import workloads as W
+
+    ws, rank, local = _dist()
+    if ws > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    build.build()
+    jz.load()
+
+    g, q, prm = W.make_workload(args.workload)
+    npts = g.npts
+    grid = jz.Grid.from_workload(g)
+    stream = torch.cuda.Stream()
+    solver = jz.Solver(grid, prm, jz.JZ_PREC_FP64, stream=stream.cuda_stream)
+    qd = torch.from_numpy(q).cuda()
+    solver.set_state(qd, 0.0)
+    torch.cuda.synchronize()
+
+    # warm-up
+    for _ in range(max(args.warmup, 0)):
+        solver.step(1, stats=False)
+    stream.synchronize()
+    solver.profile_read()                # drop warm-up counts
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    solver.profile(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    solver.step(args.steps, stats=False)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    prof = solver.profile_read()
+    solver.profile(False)
+    if ws > 1:
+        dist.barrier()
+    clocks = sampler.stop()
+    stats = solver.step(0, stats=True)   # checks the state is finite and positive
+
+    t_max = ms
+    if ws > 1:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = t.item()
+    value = ws * npts * 5 * args.steps / (t_max / 1e3) / 1e9
+
+    # end to end through the public API with pinned host buffers
+    q_host = torch.from_numpy(q).pin_memory()
+    out_host = torch.empty_like(q_host).pin_memory()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        solver.set_state(q_host, 0.0)
+        solver.step(1, stats=False)
+        solver.get_state(out_host)
+    e2e_s = (time.perf_counter() - t0) / args.e2e_steps
+    e2e_value = ws * npts * 5 / e2e_s / 1e9
+    state_bytes = 5 * npts * 8
+
+    # roofline of the dominant kernel (largest share of the timed region)
+    fp64_kinds = {k: v for k, v in prof.items() if k in FLOPS_PER_POINT and v[1] > 0}
+    top = max(fp64_kinds, key=lambda k: fp64_kinds[k][0])
+    top_ms, top_n = fp64_kinds[top]
+    pts = {"nodal": (g.ni + 4) * (g.nj + 4) * (g.nk + 4), "viscous": (g.ni + 2) * (g.nj + 2) * (g.nk + 2),
+           "faces": (g.ni + 1) * (g.nj + 1) * (g.nk + 1), "update": npts}[top]
+    achieved = FLOPS_PER_POINT[top] * pts / (top_ms / top_n / 1e3) / 1e12
+    total_prof = sum(v[0] for v in prof.values())
+    launches = int(sum(v[1] for v in prof.values()))
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        rate, secs, threads = oracle_sample_rate(2)
+        cpu = {"value": rate / 1e9, "unit": "Gpoint-stage/s", "cores": threads, "kind": "oracle",
+               "sample": f"jet {SAMPLE[0]}x{SAMPLE[1]}x{SAMPLE[2]} (same recipe, 1/15.6 of the points), 2 RK steps, "
+                         f"{secs:.1f} s"}
+
+    if rank == 0:
+        line = {
+            "metric": "Gpoint-stage updates/s", "value": value, "unit": "Gpoint-stage/s",
+            "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": t_max / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "points": npts, "dof": 5 * npts, "stages_per_step": 5,
+                       "precision": "fp64", "parallelism": f"replicas{ws}",
+                       "l2": "inputs larger than L2 (state 8 GB, metrics 16 GB per sweep)"},
+            "roofline": {"bound": "alu", "kernel": top, "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
+                         "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
+                         "traffic": TRAFFIC_PER_NODE[top] * pts if top in TRAFFIC_PER_NODE else None,
+                         "peak_source": "FP64 unit count x max SM clock (152 SMs x 4 flop/clk x 2.07 GHz)"},
+            "kernels": {k: {"ms_per_launch": v[0] / v[1], "launches": int(v[1]), "share": v[0] / total_prof}
+                        for k, v in prof.items() if v[1] > 0},
+            "gpu_launches": launches,
+            "clocks": clocks,
+            "e2e": {"value": e2e_value, "unit": "Gpoint-stage/s", "h2d_bytes_per_step": state_bytes,
+                    "d2h_bytes_per_step": state_bytes},
+            "cpu_baseline": cpu,
+            "check": {"min_rho": stats.min_rho, "min_p": stats.min_p, "t": stats.t},
+        }
+        print(json.dumps(line), flush=True)
+    solver.close()
+    grid.close()
+    if ws > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -157,6 +157,33 @@ int jz_residual(jz_solver* s, const double* q, double* rhs);
  * non-positive density or pressure. */
 int jz_rk_step(jz_solver* s, int nsteps, jz_step_stats* out);
 
+/* ---- kernel timing ---------------------------------------------------- *
+ * Kernel kinds of the stage (index of the arrays below). */
+#define JZ_PROF_NODAL    0   /* FP64 nodal pass: primitives, spectral radii, inviscid fluxes */
+#define JZ_PROF_VISCOUS  1   /* FP64 viscous pass: gradients, SGS, viscous fluxes, sensor   */
+#define JZ_PROF_FACES    2   /* FP64 dissipation face fluxes                               */
+#define JZ_PROF_UPDATE   3   /* RHS assembly and stage update                              */
+#define JZ_PROF_BC       4   /* boundary-condition kernels                                 */
+#define JZ_PROF_GHOST    5   /* ghost-point fill                                           */
+#define JZ_PROF_REDUCE   6   /* CFL, time, statistics reductions                           */
+#define JZ_PROF_FUSED32  7   /* fused FP32-flux stage kernel                               */
+#define JZ_PROF_ADJOINT  8   /* adjoint stage kernels                                      */
+#define JZ_NPROF         9
+
+/* Turn per-kernel timing on or off.  While on, the solver records a CUDA
+ * event on its stream after every kernel it launches (intervals between
+ * consecutive events are the kernels' device durations). */
+int jz_profile(jz_solver* s, int enable);
+
+/* Synchronise the solver's stream and return, per kernel kind, the summed
+ * device time in milliseconds (ms[JZ_NPROF], may be NULL) since the last
+ * read, and the number of kernel launches (launches[JZ_NPROF], may be NULL;
+ * counted whether or not timing is on).  Both are reset. */
+int jz_profile_read(jz_solver* s, double* ms, long long* launches);
+
+/* Short name of a kernel kind ("" if out of range). */
+const char* jz_profile_name(int kind);
+
 #ifdef __cplusplus
 }
 #endif

@@ -83,7 +83,18 @@ struct jz_solver {
   long long steps = 0;
   long long n_adv = 0;
   bool has_state = false;
+  // per-kernel timing: an event after every kernel while profiling is on
+  bool prof = false;
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<cudaEvent_t> ev_marks;     // recorded, in stream order
+  std::vector<int> ev_kind;              // kind of the kernel ending at each mark (-1: start)
+  double prof_ms[JZ_NPROF] = {0};
+  long long launches[JZ_NPROF] = {0};
   DevMem mem;
+  ~jz_solver() {
+    for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
+    for (cudaEvent_t e : ev_marks) cudaEventDestroy(e);
+  }
 };
 
 namespace {
@@ -137,24 +148,70 @@ int load_state(jz_solver* s, const double* src, jz::State& q) {
   return JZ_OK;
 }
 
+cudaEvent_t take_event(jz_solver* s) {
+  if (!s->ev_pool.empty()) {
+    cudaEvent_t e = s->ev_pool.back();
+    s->ev_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+  return e;
+}
+
+// Record a timing mark after a kernel of the given kind (kind -1: start mark).
+int mark(jz_solver* s, int kind) {
+  if (kind >= 0) s->launches[kind] += 1;
+  if (!s->prof) return JZ_OK;
+  cudaEvent_t e = take_event(s);
+  if (!e) return fail(JZ_ERR_CUDA, "cudaEventCreate failed");
+  JZ_CK(cudaEventRecord(e, s->st));
+  s->ev_marks.push_back(e);
+  s->ev_kind.push_back(kind);
+  return JZ_OK;
+}
+
+#define JZ_RUN(kind, call)          \
+  do {                              \
+    JZ_CK(call);                    \
+    int r_ = mark(s, (kind));       \
+    if (r_) return r_;              \
+  } while (0)
+
+int run_stage64(jz_solver* s, const jz::State& in, const jz::State& out, double alpha, int want_res,
+                double* rhs_flat) {
+  const jz::Dims& d = s->grid->d;
+  const jz::GridDev& g = s->grid->g;
+  JZ_RUN(JZ_PROF_NODAL, jz::nodal64(d, s->c, g, s->w, in, s->st));
+  JZ_RUN(JZ_PROF_VISCOUS, jz::viscous64(d, s->c, g, s->w, in, s->st));
+  JZ_RUN(JZ_PROF_FACES, jz::faces64(d, s->c, s->w, in, s->st));
+  JZ_RUN(JZ_PROF_UPDATE, jz::update64(d, g, s->w, in, s->qn, out, s->sc, alpha, want_res, rhs_flat, s->st));
+  return JZ_OK;
+}
+
 int run_step(jz_solver* s) {
   const jz::Dims& d = s->grid->d;
   const jz::GridDev& g = s->grid->g;
-  if (s->c.dt_fixed <= 0.0) JZ_CK(jz::cfl_rate(d, s->c, g, s->qn, s->sc, s->st));
-  JZ_CK(jz::set_dt(s->c, s->sc, 0, s->st));
+  if (s->c.dt_fixed <= 0.0) JZ_RUN(JZ_PROF_REDUCE, jz::cfl_rate(d, s->c, g, s->qn, s->sc, s->st));
+  JZ_RUN(JZ_PROF_REDUCE, jz::set_dt(s->c, s->sc, 0, s->st));
   jz::State in = s->qn;
   for (int l = 0; l < 5; ++l) {
     jz::State out = (l % 2 == 0) ? s->qa : s->qb;
-    JZ_CK(jz::stage64(d, s->c, g, s->w, in, s->qn, out, s->sc, kAlpha[l], l, nullptr, s->st));
-    JZ_CK(jz::apply_bcs(d, s->c, g, s->in, out, s->sc, kAlpha[l], s->st));
-    JZ_CK(jz::ghost_fill(d, out.q, 5, s->st));
+    int r = run_stage64(s, in, out, kAlpha[l], l == 0, nullptr);
+    if (r) return r;
+    if (d.topo == JZ_TOPO_JET) {
+      JZ_RUN(JZ_PROF_BC, jz::bc_farfield(d, s->c, g, out, s->st));
+      JZ_RUN(JZ_PROF_BC, jz::bc_inout(d, s->c, s->in, out, s->sc, kAlpha[l], s->st));
+      JZ_RUN(JZ_PROF_BC, jz::bc_axis(d, out, s->st));
+    }
+    JZ_RUN(JZ_PROF_GHOST, jz::ghost_fill(d, out.q, 5, s->st));
     in = out;
   }
   // Q^{n+1} is in qa (stage 5 wrote it); it becomes Q^n.
   jz::State t = s->qn;
   s->qn = s->qa;
   s->qa = t;
-  JZ_CK(jz::set_dt(s->c, s->sc, 1, s->st));
+  JZ_RUN(JZ_PROF_REDUCE, jz::set_dt(s->c, s->sc, 1, s->st));
   s->steps += 1;
   return JZ_OK;
 }
@@ -378,7 +435,12 @@ int jz_residual(jz_solver* s, const double* q, double* rhs) {
     if (r) return r;
     dst = s->staging;
   }
-  JZ_CK(jz::stage64(d, s->c, s->grid->g, s->w, s->qb, s->qb, s->qb, s->sc, 0.0, -1, dst, s->st));
+  if (s->prof) {
+    r = mark(s, -1);
+    if (r) return r;
+  }
+  r = run_stage64(s, s->qb, s->qb, 0.0, 0, dst);
+  if (r) return r;
   if (!dev) {
     JZ_CK(cudaMemcpyAsync(rhs, dst, 5 * sizeof(double) * npts(d), cudaMemcpyDeviceToHost, s->st));
     JZ_CK(cudaStreamSynchronize(s->st));
@@ -390,12 +452,17 @@ int jz_rk_step(jz_solver* s, int nsteps, jz_step_stats* out) {
   if (!s) return fail(JZ_ERR_ARG, "jz_rk_step: NULL solver");
   if (nsteps < 0) return fail(JZ_ERR_ARG, "jz_rk_step: nsteps < 0");
   if (!s->has_state) return fail(JZ_ERR_STATE, "jz_rk_step: no state set");
+  if (s->prof && nsteps > 0) {
+    int r = mark(s, -1);
+    if (r) return r;
+  }
   for (int n = 0; n < nsteps; ++n) {
     int r = run_step(s);
     if (r) return r;
   }
   if (!out) return JZ_OK;
   const jz::Dims& d = s->grid->d;
+  s->launches[JZ_PROF_REDUCE] += 2;
   JZ_CK(jz::stats_with(d, s->c, s->grid->g, s->qn, s->sc, s->part, s->st));
   jz::Scalars h;
   JZ_CK(cudaMemcpyAsync(&h, s->sc, sizeof h, cudaMemcpyDeviceToHost, s->st));
@@ -409,6 +476,40 @@ int jz_rk_step(jz_solver* s, int nsteps, jz_step_stats* out) {
   out->steps = s->steps;
   if (h.nonfinite) return fail(JZ_ERR_NONFINITE, "state holds NaN/Inf or non-positive density/pressure");
   return JZ_OK;
+}
+
+int jz_profile(jz_solver* s, int enable) {
+  if (!s) return fail(JZ_ERR_ARG, "jz_profile: NULL solver");
+  s->prof = enable != 0;
+  return JZ_OK;
+}
+
+int jz_profile_read(jz_solver* s, double* ms, long long* launches) {
+  if (!s) return fail(JZ_ERR_ARG, "jz_profile_read: NULL solver");
+  JZ_CK(cudaStreamSynchronize(s->st));
+  for (size_t i = 1; i < s->ev_marks.size(); ++i) {
+    const int kind = s->ev_kind[i];
+    if (kind < 0) continue;
+    float t = 0.f;
+    JZ_CK(cudaEventElapsedTime(&t, s->ev_marks[i - 1], s->ev_marks[i]));
+    s->prof_ms[kind] += t;
+  }
+  for (cudaEvent_t e : s->ev_marks) s->ev_pool.push_back(e);
+  s->ev_marks.clear();
+  s->ev_kind.clear();
+  for (int k = 0; k < JZ_NPROF; ++k) {
+    if (ms) ms[k] = s->prof_ms[k];
+    if (launches) launches[k] = s->launches[k];
+    s->prof_ms[k] = 0.0;
+    s->launches[k] = 0;
+  }
+  return JZ_OK;
+}
+
+const char* jz_profile_name(int kind) {
+  static const char* names[JZ_NPROF] = {"nodal", "viscous", "faces", "update", "bc", "ghost", "reduce",
+                                        "fused32", "adjoint"};
+  return (kind >= 0 && kind < JZ_NPROF) ? names[kind] : "";
 }
 
 }  // extern "C"

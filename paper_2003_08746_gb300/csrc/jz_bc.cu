@@ -147,13 +147,20 @@ __global__ void k_build_inflow(Dims d, Consts c, GridDev g, double* u0, double* 
 
 }  // namespace
 
-cudaError_t apply_bcs(const Dims& d, const Consts& c, const GridDev& g, const Inflow& in, const State& q,
-                      const Scalars* sc, double alpha, cudaStream_t st) {
-  if (d.topo != JZ_TOPO_JET) return cudaSuccess;
+cudaError_t bc_farfield(const Dims& d, const Consts& c, const GridDev& g, const State& q, cudaStream_t st) {
   const long long nf = (long long)(d.ni - 2) * d.nk;
   k_farfield<<<blocks_for(nf, kTPB), kTPB, 0, st>>>(d, c, g, q);
+  return cudaGetLastError();
+}
+
+cudaError_t bc_inout(const Dims& d, const Consts& c, const Inflow& in, const State& q, const Scalars* sc,
+                     double alpha, cudaStream_t st) {
   const long long nio = 2LL * (d.nj - 1) * d.nk;
   k_inout<<<blocks_for(nio, kTPB), kTPB, 0, st>>>(d, c, in, q, sc, alpha);
+  return cudaGetLastError();
+}
+
+cudaError_t bc_axis(const Dims& d, const State& q, cudaStream_t st) {
   k_axis<<<d.ni, kTPB, 0, st>>>(d, q);
   return cudaGetLastError();
 }

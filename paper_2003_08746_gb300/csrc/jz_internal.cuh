@@ -111,13 +111,21 @@ cudaError_t pack_real(const Dims& d, double* const* padded, const double* flat, 
                       cudaStream_t st);
 cudaError_t unpack_real(const Dims& d, double* const* padded, double* flat, int nvar,
                         cudaStream_t st);
-// FP64 stage passes
-cudaError_t stage64(const Dims& d, const Consts& c, const GridDev& g, const Work64& w,
-                    const State& qin, const State& qn, const State& qout, const Scalars* sc,
-                    double alpha, int stage, double* rhs_flat, cudaStream_t st);
-// boundary conditions (jet)
-cudaError_t apply_bcs(const Dims& d, const Consts& c, const GridDev& g, const Inflow& in,
-                      const State& q, const Scalars* sc, double alpha, cudaStream_t st);
+// FP64 stage passes (one kernel each)
+cudaError_t nodal64(const Dims& d, const Consts& c, const GridDev& g, const Work64& w, const State& qin,
+                    cudaStream_t st);
+cudaError_t viscous64(const Dims& d, const Consts& c, const GridDev& g, const Work64& w, const State& qin,
+                      cudaStream_t st);
+cudaError_t faces64(const Dims& d, const Consts& c, const Work64& w, const State& qin, cudaStream_t st);
+// stage update (rhs_flat == nullptr) or RHS output to rhs_flat [5][N]
+cudaError_t update64(const Dims& d, const GridDev& g, const Work64& w, const State& qin, const State& qn,
+                     const State& qout, const Scalars* sc, double alpha, int want_res, double* rhs_flat,
+                     cudaStream_t st);
+// boundary conditions (jet), in this order after every stage
+cudaError_t bc_farfield(const Dims& d, const Consts& c, const GridDev& g, const State& q, cudaStream_t st);
+cudaError_t bc_inout(const Dims& d, const Consts& c, const Inflow& in, const State& q, const Scalars* sc,
+                     double alpha, cudaStream_t st);
+cudaError_t bc_axis(const Dims& d, const State& q, cudaStream_t st);
 cudaError_t build_inflow(const Dims& d, const Consts& c, const GridDev& g, const jz_params& p,
                          Inflow& in, cudaStream_t st);
 // reductions

@@ -205,21 +205,35 @@ __global__ void __launch_bounds__(kTPB) k_update(Dims d, GridDev g, Work64 w, St
 
 }  // namespace
 
-cudaError_t stage64(const Dims& d, const Consts& c, const GridDev& g, const Work64& w, const State& qin,
-                    const State& qn, const State& qout, const Scalars* sc, double alpha, int stage,
-                    double* rhs_flat, cudaStream_t st) {
+cudaError_t nodal64(const Dims& d, const Consts& c, const GridDev& g, const Work64& w, const State& qin,
+                    cudaStream_t st) {
   const long long n0 = (long long)(d.ni + 2 * kG) * (d.nj + 2 * kG) * (d.nk + 2 * kG);
-  const long long n1 = (long long)(d.ni + 2) * (d.nj + 2) * (d.nk + 2);
-  const long long nf = (long long)(d.ni + 1) * (d.nj + 1) * (d.nk + 1);
-  const long long nr = (long long)d.ni * d.nj * d.nk;
   k_nodal<<<blocks_for(n0, kTPB), kTPB, 0, st>>>(d, c, g, w, qin);
+  return cudaGetLastError();
+}
+
+cudaError_t viscous64(const Dims& d, const Consts& c, const GridDev& g, const Work64& w, const State& qin,
+                      cudaStream_t st) {
+  const long long n1 = (long long)(d.ni + 2) * (d.nj + 2) * (d.nk + 2);
   k_viscous<<<blocks_for(n1, kTPB), kTPB, 0, st>>>(d, c, g, w, qin);
+  return cudaGetLastError();
+}
+
+cudaError_t faces64(const Dims& d, const Consts& c, const Work64& w, const State& qin, cudaStream_t st) {
+  const long long nf = (long long)(d.ni + 1) * (d.nj + 1) * (d.nk + 1);
   k_faces<<<blocks_for(nf, kTPB), kTPB, 0, st>>>(d, c, w, qin);
+  return cudaGetLastError();
+}
+
+cudaError_t update64(const Dims& d, const GridDev& g, const Work64& w, const State& qin, const State& qn,
+                     const State& qout, const Scalars* sc, double alpha, int want_res, double* rhs_flat,
+                     cudaStream_t st) {
+  const long long nr = (long long)d.ni * d.nj * d.nk;
   double* res_sum = const_cast<double*>(&sc->res_sum);
   if (rhs_flat)
     k_update<1><<<blocks_for(nr, kTPB), kTPB, 0, st>>>(d, g, w, qin, qn, qout, sc, alpha, 0, rhs_flat, res_sum);
   else
-    k_update<0><<<blocks_for(nr, kTPB), kTPB, 0, st>>>(d, g, w, qin, qn, qout, sc, alpha, stage == 0, nullptr,
+    k_update<0><<<blocks_for(nr, kTPB), kTPB, 0, st>>>(d, g, w, qin, qn, qout, sc, alpha, want_res, nullptr,
                                                        res_sum);
   return cudaGetLastError();
 }

@@ -26,7 +26,8 @@ N_MODES, N_FREQ = 8, 4
 # Entry points declared in include/jz.h (checked by the tests).
 EXPORTS = ("jz_last_error", "jz_version", "jz_create_grid", "jz_destroy_grid", "jz_compute_metrics",
            "jz_get_metrics", "jz_create", "jz_destroy", "jz_set_state", "jz_get_state", "jz_residual",
-           "jz_rk_step")
+           "jz_rk_step", "jz_profile", "jz_profile_read", "jz_profile_name")
+JZ_NPROF = 9
 
 
 class JzError(RuntimeError):
@@ -78,6 +79,9 @@ def load(path: str | None = None) -> ctypes.CDLL:
         "jz_get_state": ([vp, vp], i),
         "jz_residual": ([vp, vp, vp], i),
         "jz_rk_step": ([vp, i, ctypes.POINTER(jz_step_stats)], i),
+        "jz_profile": ([vp, i], i),
+        "jz_profile_read": ([vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong)], i),
+        "jz_profile_name": ([i], ctypes.c_char_p),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -174,6 +178,19 @@ def jz_rk_step(h, nsteps: int, want_stats: bool = True):
     return st
 
 
+def jz_profile(h, enable: bool):
+    _check(load().jz_profile(h, 1 if enable else 0))
+
+
+def jz_profile_read(h):
+    """{kind name: (device ms, launches)} since the last read."""
+    ms = (ctypes.c_double * JZ_NPROF)()
+    n = (ctypes.c_longlong * JZ_NPROF)()
+    _check(load().jz_profile_read(h, ms, n))
+    lib = load()
+    return {lib.jz_profile_name(k).decode(): (ms[k], n[k]) for k in range(JZ_NPROF)}
+
+
 # --- owners ----------------------------------------------------------------
 class Grid:
     """Owner of a jz_grid handle; metrics are computed on construction."""
@@ -234,6 +251,12 @@ class Solver:
 
     def step(self, nsteps: int = 1, stats: bool = True):
         return jz_rk_step(self.h, nsteps, stats)
+
+    def profile(self, enable: bool = True):
+        jz_profile(self.h, enable)
+
+    def profile_read(self):
+        return jz_profile_read(self.h)
 
     def close(self):
         if self.h:
