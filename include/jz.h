@@ -184,6 +184,31 @@ int jz_profile_read(jz_solver* s, double* ms, long long* launches);
 /* Short name of a kernel kind ("" if out of range). */
 const char* jz_profile_name(int kind);
 
+/* ---- allocation-free residual ------------------------------------------- *
+ * The paper has no counterpart to this entry point; it is a service for
+ * callers that cannot have the library allocate device memory: code whose
+ * device memory belongs to another allocator under a fixed budget, and
+ * latency-critical loops that cannot absorb cudaMalloc/cudaFree (cudaFree
+ * synchronises the whole device).
+ *
+ * Same result as jz_residual (FP64 form) for the state q on grid g, with
+ * parameters p (p->precision must be JZ_PREC_FP64).  q [5][N] and rhs [5][N]
+ * are caller-owned DEVICE pointers; the work is queued on `stream` (a
+ * cudaStream_t, NULL = legacy default stream) and the call returns without
+ * waiting for it.  No device memory is allocated: the scratch is a fixed
+ * array of JZ_NOALLOC_SCRATCH_BYTES inside the library, present on every
+ * GPU that loads the library until the process exits.  A grid needs
+ * 256 + 47 * 8 * (padded nodes) bytes, padded nodes = round4(ni+4) *
+ * (nj+4) * (nk+4) (about 178,000 padded nodes, e.g. 48 x 48 x 48 real
+ * nodes); larger grids are rejected with JZ_ERR_ARG and a message giving
+ * the limit.  The first call on a device looks up the scratch address (make
+ * it before any stream capture).  All calls on a device share the scratch:
+ * calls whose kernels overlap on the GPU race; keep them on one stream.
+ * Errors: JZ_ERR_ARG (NULL/host pointers, bad parameters, grid too large),
+ * JZ_ERR_STATE (metrics not computed), JZ_ERR_CUDA. */
+#define JZ_NOALLOC_SCRATCH_BYTES (64u * 1024u * 1024u)
+int jz_residual_noalloc(const jz_grid* g, const jz_params* p, const double* q, double* rhs, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

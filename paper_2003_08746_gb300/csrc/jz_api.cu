@@ -99,29 +99,6 @@ struct jz_solver {
 
 namespace {
 
-jz::Consts make_consts(const jz_params& p) {
-  jz::Consts c;
-  c.gamma = p.gamma;
-  c.gm1 = p.gamma - 1.0;
-  c.Cp = 1.0 / c.gm1;
-  c.mu_ref = p.mach_ref / p.Re;
-  c.S_hat = p.S1_K / p.T_ref_K;
-  c.sut_num = 1.0 + c.S_hat;
-  c.k_lam = c.Cp / p.Pr;
-  c.k_sgs = c.Cp / p.Pr_sgs;
-  c.C_s = p.C_s;
-  c.kappa2 = p.kappa2;
-  c.kappa4 = p.kappa4;
-  c.sigma = p.sigma;
-  c.sigma_is_two_thirds = std::fabs(p.sigma - 2.0 / 3.0) < 1e-15 ? 1 : 0;
-  c.cfl = p.cfl;
-  c.dt_fixed = p.dt_fixed;
-  c.p_inf = 1.0 / p.gamma;
-  c.jet_mach = p.jet_mach;
-  c.theta_mom = p.theta_mom;
-  return c;
-}
-
 long long npts(const jz::Dims& d) { return (long long)d.ni * d.nj * d.nk; }
 
 int ensure_staging(jz_solver* s) {
@@ -217,6 +194,19 @@ int run_step(jz_solver* s) {
 }
 
 }  // namespace
+
+namespace jz {
+
+int set_error(int code, const char* msg) { return fail(code, "%s", msg); }
+
+bool grid_view(const jz_grid* g, Dims* d, GridDev* dev) {
+  if (!g || !g->metrics) return false;
+  *d = g->d;
+  *dev = g->g;
+  return true;
+}
+
+}  // namespace jz
 
 extern "C" {
 
@@ -339,7 +329,7 @@ int jz_create(jz_grid* g, const jz_params* p, void* stream, jz_solver** out) {
   if (!s) return fail(JZ_ERR_OOM, "host allocation failed");
   s->grid = g;
   s->prm = *p;
-  s->c = make_consts(*p);
+  s->c = jz::make_consts(*p);
   s->st = static_cast<cudaStream_t>(stream);
   const jz::Dims& d = g->d;
   cudaError_t e = cudaSuccess;

@@ -64,6 +64,30 @@ struct Consts {
   double jet_mach, theta_mom;
 };
 
+// Derived constants from the caller's parameters.
+inline Consts make_consts(const jz_params& p) {
+  Consts c;
+  c.gamma = p.gamma;
+  c.gm1 = p.gamma - 1.0;
+  c.Cp = 1.0 / c.gm1;
+  c.mu_ref = p.mach_ref / p.Re;
+  c.S_hat = p.S1_K / p.T_ref_K;
+  c.sut_num = 1.0 + c.S_hat;
+  c.k_lam = c.Cp / p.Pr;
+  c.k_sgs = c.Cp / p.Pr_sgs;
+  c.C_s = p.C_s;
+  c.kappa2 = p.kappa2;
+  c.kappa4 = p.kappa4;
+  c.sigma = p.sigma;
+  c.sigma_is_two_thirds = fabs(p.sigma - 2.0 / 3.0) < 1e-15 ? 1 : 0;
+  c.cfl = p.cfl;
+  c.dt_fixed = p.dt_fixed;
+  c.p_inf = 1.0 / p.gamma;
+  c.jet_mach = p.jet_mach;
+  c.theta_mom = p.theta_mom;
+  return c;
+}
+
 // Device scalars of a solver (one allocation).
 struct Scalars {
   double t;          // time at the start of the current step
@@ -136,6 +160,12 @@ int stat_partial_count();
 cudaError_t stats_with(const Dims& d, const Consts& c, const GridDev& g, const State& q, Scalars* sc,
                        double* part, cudaStream_t st);
 cudaError_t check_volume(const Dims& d, const GridDev& g, int* bad, cudaStream_t st);
+
+// ---- shared with the C ABI layer ------------------------------------------
+// Record an error message for jz_last_error(); returns code.
+int set_error(int code, const char* msg);
+// Dimensions and device arrays of a grid whose metrics are computed.
+bool grid_view(const jz_grid* g, Dims* d, GridDev* dev);
 
 // ---- helpers ------------------------------------------------------------
 inline unsigned blocks_for(long long n, int tpb) { return (unsigned)((n + tpb - 1) / tpb); }

@@ -26,7 +26,8 @@ N_MODES, N_FREQ = 8, 4
 # Entry points declared in include/jz.h (checked by the tests).
 EXPORTS = ("jz_last_error", "jz_version", "jz_create_grid", "jz_destroy_grid", "jz_compute_metrics",
            "jz_get_metrics", "jz_create", "jz_destroy", "jz_set_state", "jz_get_state", "jz_residual",
-           "jz_rk_step", "jz_profile", "jz_profile_read", "jz_profile_name")
+           "jz_rk_step", "jz_profile", "jz_profile_read", "jz_profile_name", "jz_residual_noalloc")
+JZ_NOALLOC_SCRATCH_BYTES = 64 * 1024 * 1024
 JZ_NPROF = 9
 
 
@@ -82,6 +83,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
         "jz_profile": ([vp, i], i),
         "jz_profile_read": ([vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong)], i),
         "jz_profile_name": ([i], ctypes.c_char_p),
+        "jz_residual_noalloc": ([vp, ctypes.POINTER(jz_params), vp, vp, vp], i),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -170,6 +172,12 @@ def jz_get_state(h, q):
 
 def jz_residual(h, q, rhs):
     _check(load().jz_residual(h, _ptr(q), _ptr(rhs)))
+
+
+def jz_residual_noalloc(grid_h, params: jz_params, q, rhs, stream=None):
+    """Residual with the library's fixed scratch array (no device allocation); device q and rhs."""
+    st = ctypes.c_void_p(0 if stream is None else int(stream))
+    _check(load().jz_residual_noalloc(grid_h, ctypes.byref(params), _ptr(q), _ptr(rhs), st))
 
 
 def jz_rk_step(h, nsteps: int, want_stats: bool = True):
