@@ -99,6 +99,26 @@ def cbrt(x: torch.Tensor) -> torch.Tensor:
     return _Cbrt.apply(x)
 
 
+class _Sqrt0(torch.autograd.Function):
+    """sqrt with derivative 1/(2 sqrt(x)), taken as 0 at x = 0 (subgradient convention)."""
+
+    @staticmethod
+    def forward(ctx, x):
+        s = torch.sqrt(x)
+        ctx.save_for_backward(s)
+        return s
+
+    @staticmethod
+    def backward(ctx, g):
+        (s,) = ctx.saved_tensors
+        safe = torch.where(s > 0, s, torch.ones_like(s))
+        return torch.where(s > 0, g / (2.0 * safe), torch.zeros_like(s))
+
+
+def sqrt0(x: torch.Tensor) -> torch.Tensor:
+    return _Sqrt0.apply(x)
+
+
 # ---------------------------------------------------------------------------
 # Parameters (derived constants computed here, independently of the library)
 # ---------------------------------------------------------------------------
@@ -347,7 +367,7 @@ def viscous_fluxes(grid: Grid, rho, u, v, w, T, c: Consts):
     Sij = [[0.5 * (L[i][j] + L[j][i]) for j in range(3)] for i in range(3)]
     div = Sij[0][0] + Sij[1][1] + Sij[2][2]
     SS = sum(Sij[i][j] * Sij[i][j] for i in range(3) for j in range(3))
-    Smod = torch.sqrt(2.0 * SS)
+    Smod = sqrt0(2.0 * SS)
     mu = sutherland(T, c)
     mu_sgs = rho * (c.C_s * grid.Delta) ** 2 * Smod
     mu_eff = mu + mu_sgs
@@ -609,6 +629,71 @@ def residual_l2(grid: Grid, R):
     """RMS over updated nodes of the density residual."""
     r = R[0][grid.updated]
     return torch.sqrt((r * r).mean())
+
+
+# ---------------------------------------------------------------------------
+# Observer functional and its discrete adjoint (reverse sweep by autograd)
+# ---------------------------------------------------------------------------
+class Observer:
+    """Cylindrical observer surface r = r_obs of a jet grid.
+
+    Pressure on the surface is interpolated linearly in r between the
+    bracketing grid lines j_o, j_o + 1 (the radial coordinate of a jet grid
+    depends on j only); the surface weights are w_ik = r_obs dtheta dx_i with
+    the trapezoid dx_i of the axial coordinate.
+    """
+
+    def __init__(self, grid: Grid, r_obs: float):
+        X = real(grid.xyz_p)
+        r = torch.sqrt(X[1, 0, :, 0] ** 2 + X[2, 0, :, 0] ** 2)       # r_j at i = 0, k = 0
+        below = (r <= r_obs).nonzero().flatten()
+        self.j0 = int(below.max())
+        if self.j0 >= grid.nj - 1:
+            raise ValueError("observer radius beyond the far field")
+        self.beta = float((r_obs - r[self.j0]) / (r[self.j0 + 1] - r[self.j0]))
+        x = X[0, 0, 0, :]
+        dx = torch.empty_like(x)
+        dx[1:-1] = 0.5 * (x[2:] - x[:-2])
+        dx[0] = 0.5 * (x[1] - x[0])
+        dx[-1] = 0.5 * (x[-1] - x[-2])
+        self.w = (r_obs * (2.0 * math.pi / grid.nk)) * dx              # [ni], same for every k
+
+    def value(self, Q, c: Consts):
+        """sum_{i,k} w_ik (p~_ik - p_inf)^2 for one state Q."""
+        def pres(q):
+            return c.gm1 * (q[4] - 0.5 * (q[1] * q[1] + q[2] * q[2] + q[3] * q[3]) / q[0])
+        p0 = pres(Q[:, :, self.j0, :])
+        p1 = pres(Q[:, :, self.j0 + 1, :])
+        pt = (1.0 - self.beta) * p0 + self.beta * p1
+        return (self.w * (pt - c.p_inf) ** 2).sum()
+
+
+def functional(grid: Grid, Q0, c: Consts, amps, nsteps: int, dt, obs: Observer, t0: float = 0.0):
+    """J = sum_{n=1..N} dt sum_ik w_ik (p~_ik(Q^n) - p_inf)^2 with the forcing amplitudes `amps`
+    ([8][4]) and a frozen time step dt; each step is recomputed in the backward pass."""
+    from torch.utils.checkpoint import checkpoint
+    c.amp = amps
+    dt = torch.as_tensor(dt, dtype=DT)
+    Q = Q0
+    J = torch.zeros((), dtype=DT)
+    for n in range(nsteps):
+        t = torch.as_tensor(t0 + n * float(dt), dtype=DT)
+        Q = checkpoint(lambda q, a, t=t: rk_step(grid, q, c, t, dt=dt)[0], Q, amps, use_reentrant=False)
+        J = J + dt * obs.value(Q, c)
+    return J
+
+
+def functional_gradient(grid: Grid, Q0, c: Consts, amps, nsteps: int, dt, obs: Observer, t0: float = 0.0):
+    """(J, dJ/dA) by reverse-mode differentiation of the discrete forward map (the oracle's reverse sweep)."""
+    old = FILL
+    set_fill(0.0)                     # keep shifted-in entries finite for the backward pass
+    try:
+        A = torch.as_tensor(amps, dtype=DT).clone().requires_grad_(True)
+        J = functional(grid, Q0, c, A, nsteps, dt, obs, t0)
+        (g,) = torch.autograd.grad(J, A)
+    finally:
+        set_fill(old)
+    return J.detach(), g
 
 
 def make(xyz, ni, nj, nk, topology, period, prm):

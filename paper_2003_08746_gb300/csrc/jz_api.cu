@@ -76,6 +76,10 @@ struct jz_solver {
   cudaStream_t st = nullptr;
   jz::State qn, qa, qb;
   jz::Work64 w;
+  bool fp32 = false;              // JZ_PREC_FP32FLUX form
+  float* Sf[10] = {nullptr};      // FP32 metrics (FP32-flux form)
+  int kchunk = 0;                 // k planes per CTA of the fused kernel
+  bool rate_ready = false;        // a CFL rate of Q^n is in Scalars::rate_max
   jz::Scalars* sc = nullptr;
   jz::Inflow in;
   double* part = nullptr;
@@ -169,12 +173,20 @@ int run_stage64(jz_solver* s, const jz::State& in, const jz::State& out, double 
 int run_step(jz_solver* s) {
   const jz::Dims& d = s->grid->d;
   const jz::GridDev& g = s->grid->g;
-  if (s->c.dt_fixed <= 0.0) JZ_RUN(JZ_PROF_REDUCE, jz::cfl_rate(d, s->c, g, s->qn, s->sc, s->st));
+  // The FP32-flux stage 5 leaves the CFL rate of Q^{n+1} behind; otherwise
+  // (FP64 form, or first step after jz_set_state) it is reduced here.
+  if (s->c.dt_fixed <= 0.0 && !(s->fp32 && s->rate_ready))
+    JZ_RUN(JZ_PROF_REDUCE, jz::cfl_rate(d, s->c, g, s->qn, s->sc, s->st));
   JZ_RUN(JZ_PROF_REDUCE, jz::set_dt(s->c, s->sc, 0, s->st));
   jz::State in = s->qn;
   for (int l = 0; l < 5; ++l) {
     jz::State out = (l % 2 == 0) ? s->qa : s->qb;
-    int r = run_stage64(s, in, out, kAlpha[l], l == 0, nullptr);
+    int r = JZ_OK;
+    if (s->fp32)
+      JZ_RUN(JZ_PROF_FUSED32, jz::fused32(d, s->c, s->Sf, in, s->qn, out, s->sc, kAlpha[l], l == 0,
+                                          l == 4 && s->c.dt_fixed <= 0.0, nullptr, s->kchunk, s->st));
+    else
+      r = run_stage64(s, in, out, kAlpha[l], l == 0, nullptr);
     if (r) return r;
     if (d.topo == JZ_TOPO_JET) {
       JZ_RUN(JZ_PROF_BC, jz::bc_farfield(d, s->c, g, out, s->st));
@@ -190,6 +202,7 @@ int run_step(jz_solver* s) {
   s->qa = t;
   JZ_RUN(JZ_PROF_REDUCE, jz::set_dt(s->c, s->sc, 1, s->st));
   s->steps += 1;
+  s->rate_ready = s->fp32 && s->c.dt_fixed <= 0.0;
   return JZ_OK;
 }
 
@@ -324,7 +337,8 @@ int jz_create(jz_grid* g, const jz_params* p, void* stream, jz_solver** out) {
       !(p->S1_K >= 0.0) || !(p->C_s >= 0.0) || !(p->kappa2 >= 0.0) || !(p->kappa4 >= 0.0) ||
       !(p->sigma > 0.0 && p->sigma < 1.0) || !(p->cfl > 0.0) || !(p->dt_fixed >= 0.0))
     return fail(JZ_ERR_ARG, "jz_create: parameter out of range");
-  if (p->precision != JZ_PREC_FP64) return fail(JZ_ERR_ARG, "jz_create: precision %d not available", p->precision);
+  if (p->precision != JZ_PREC_FP64 && p->precision != JZ_PREC_FP32FLUX)
+    return fail(JZ_ERR_ARG, "jz_create: unknown precision %d", p->precision);
   jz_solver* s = new (std::nothrow) jz_solver;
   if (!s) return fail(JZ_ERR_OOM, "host allocation failed");
   s->grid = g;
@@ -342,13 +356,31 @@ int jz_create(jz_grid* g, const jz_params* p, void* stream, jz_solver** out) {
     A(s->qa.q[m], d.Np);
     A(s->qb.q[m], d.Np);
   }
-  A(s->w.u, d.Np); A(s->w.v, d.Np); A(s->w.w, d.Np); A(s->w.T, d.Np); A(s->w.p, d.Np); A(s->w.mu, d.Np);
-  for (int dir = 0; dir < 3; ++dir) {
-    A(s->w.Lam[dir], d.Np);
-    A(s->w.nu[dir], d.Np);
-    for (int m = 0; m < 5; ++m) {
-      A(s->w.H[dir][m], d.Np);
-      A(s->w.D[dir][m], d.Np);
+  s->fp32 = p->precision == JZ_PREC_FP32FLUX;
+  float** Sf_dev = nullptr;
+  if (s->fp32) {
+    for (int i = 0; i < 10; ++i) {
+      double* tmp = nullptr;
+      A(tmp, (d.Np + 1) / 2);            // Np floats
+      s->Sf[i] = reinterpret_cast<float*>(tmp);
+    }
+    double* tmp = nullptr;
+    A(tmp, 10);
+    Sf_dev = reinterpret_cast<float**>(tmp);
+    // CTAs of 30 x 8 columns; split k so that the grid covers the SMs evenly
+    const long long tiles = (long long)((d.ni + 29) / 30) * ((d.nj + 7) / 8);
+    int nch = 1;
+    while (tiles * nch < 8 * 304 && nch < d.nk / 16) nch *= 2;
+    s->kchunk = (d.nk + nch - 1) / nch;
+  } else {
+    A(s->w.u, d.Np); A(s->w.v, d.Np); A(s->w.w, d.Np); A(s->w.T, d.Np); A(s->w.p, d.Np); A(s->w.mu, d.Np);
+    for (int dir = 0; dir < 3; ++dir) {
+      A(s->w.Lam[dir], d.Np);
+      A(s->w.nu[dir], d.Np);
+      for (int m = 0; m < 5; ++m) {
+        A(s->w.H[dir][m], d.Np);
+        A(s->w.D[dir][m], d.Np);
+      }
     }
   }
   double* scal = nullptr;
@@ -362,6 +394,15 @@ int jz_create(jz_grid* g, const jz_params* p, void* stream, jz_solver** out) {
   if (e != cudaSuccess) {
     delete s;
     return fail(JZ_ERR_OOM, "jz_create: device allocation failed: %s", cudaGetErrorString(e));
+  }
+  if (s->fp32) {
+    e = cudaMemcpy(Sf_dev, s->Sf, sizeof(s->Sf), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = jz::metrics_to_f32(d, g->g, Sf_dev, s->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->st);
+    if (e != cudaSuccess) {
+      delete s;
+      return fail(JZ_ERR_CUDA, "jz_create: FP32 metrics: %s", cudaGetErrorString(e));
+    }
   }
   if (d.topo == JZ_TOPO_JET) {
     e = jz::build_inflow(d, s->c, g->g, *p, s->in, s->st);
@@ -393,6 +434,7 @@ int jz_set_state(jz_solver* s, const double* q, double t) {
   JZ_CK(cudaMemcpyAsync(s->sc, &h, sizeof h, cudaMemcpyHostToDevice, s->st));
   JZ_CK(cudaStreamSynchronize(s->st));
   s->steps = 0;
+  s->rate_ready = false;
   s->has_state = true;
   return JZ_OK;
 }
@@ -429,8 +471,13 @@ int jz_residual(jz_solver* s, const double* q, double* rhs) {
     r = mark(s, -1);
     if (r) return r;
   }
-  r = run_stage64(s, s->qb, s->qb, 0.0, 0, dst);
-  if (r) return r;
+  if (s->fp32) {
+    JZ_RUN(JZ_PROF_FUSED32, jz::fused32(d, s->c, s->Sf, s->qb, s->qb, s->qb, s->sc, 0.0, 0, 0, dst, s->kchunk,
+                                        s->st));
+  } else {
+    r = run_stage64(s, s->qb, s->qb, 0.0, 0, dst);
+    if (r) return r;
+  }
   if (!dev) {
     JZ_CK(cudaMemcpyAsync(rhs, dst, 5 * sizeof(double) * npts(d), cudaMemcpyDeviceToHost, s->st));
     JZ_CK(cudaStreamSynchronize(s->st));

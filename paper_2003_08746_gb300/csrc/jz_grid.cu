@@ -128,15 +128,54 @@ __global__ void k_derived(Dims d, Ptrs16 M, Ptrs16 out) {
   out.p[4][p] = cbrt(V);
 }
 
+// Ghost shell enumerated directly: the four k-ghost planes (with their i/j
+// ghosts), then the four j-ghost rows of every real k, then the four i-ghost
+// columns of every real (j, k).  Every ghost copies from a real node.
+__device__ __forceinline__ bool ghost_coord(const Dims& d, long long t, int& i, int& j, int& k) {
+  const long long ei = d.ni + 2 * kG, ej = d.nj + 2 * kG;
+  const long long nA = 4 * ei * ej, nB = 4 * ei * d.nk, nC = 4LL * d.nj * d.nk;
+  if (t < nA) {
+    i = (int)(t % ei) - kG;
+    const long long r = t / ei;
+    j = (int)(r % ej) - kG;
+    const int s = (int)(r / ej);                 // 0..3
+    k = s < 2 ? s - 2 : d.nk + s - 2;
+    return true;
+  }
+  t -= nA;
+  if (t < nB) {
+    i = (int)(t % ei) - kG;
+    const long long r = t / ei;
+    const int s = (int)(r % 4);
+    k = (int)(r / 4);
+    j = s < 2 ? s - 2 : d.nj + s - 2;
+    return true;
+  }
+  t -= nB;
+  if (t < nC) {
+    const int s = (int)(t % 4);
+    const long long r = t / 4;
+    j = (int)(r % d.nj);
+    k = (int)(r / d.nj);
+    i = s < 2 ? s - 2 : d.ni + s - 2;
+    return true;
+  }
+  return false;
+}
+
 __global__ void k_ghost_fill(Dims d, Ptrs16 f, int nvar) {
-  Box b{-kG, -kG, -kG, d.ni + 2 * kG, d.nj + 2 * kG, d.nk + 2 * kG};
   int i, j, k;
-  if (!box_coord(b, blockIdx.x * (long long)blockDim.x + threadIdx.x, i, j, k)) return;
-  if (i >= 0 && i < d.ni && j >= 0 && j < d.nj && k >= 0 && k < d.nk) return;
+  if (!ghost_coord(d, blockIdx.x * (long long)blockDim.x + threadIdx.x, i, j, k)) return;
   int si, sj, sk;
   ghost_source(d, i, j, k, si, sj, sk);
   const long long p = pidx(d, i, j, k), q = pidx(d, si, sj, sk);
   for (int v = 0; v < nvar; ++v) f.p[v][p] = f.p[v][q];
+}
+
+__global__ void k_to_f32(Dims d, Ptrs16 src, float* const* dst, int nvar) {
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= d.Np) return;
+  for (int v = 0; v < nvar; ++v) dst[v][t] = __double2float_rn(src.p[v][t]);
 }
 
 __global__ void k_pack(Dims d, Ptrs16 padded, const double* __restrict__ flat, int nvar) {
@@ -213,8 +252,17 @@ cudaError_t check_volume(const Dims& d, const GridDev& g, int* bad, cudaStream_t
 }
 
 cudaError_t ghost_fill(const Dims& d, double* const* f, int nvar, cudaStream_t st) {
-  const long long np = (long long)(d.ni + 2 * kG) * (d.nj + 2 * kG) * (d.nk + 2 * kG);
-  k_ghost_fill<<<blocks_for(np, kTPB), kTPB, 0, st>>>(d, ptrs(f, nvar), nvar);
+  const long long ei = d.ni + 2 * kG, ej = d.nj + 2 * kG;
+  const long long ng = 4 * ei * ej + 4 * ei * d.nk + 4LL * d.nj * d.nk;
+  k_ghost_fill<<<blocks_for(ng, kTPB), kTPB, 0, st>>>(d, ptrs(f, nvar), nvar);
+  return cudaGetLastError();
+}
+
+cudaError_t metrics_to_f32(const Dims& d, const GridDev& g, float* const* dst_dev, cudaStream_t st) {
+  double* M[10];
+  for (int i = 0; i < 9; ++i) M[i] = g.S[i];
+  M[9] = g.V;
+  k_to_f32<<<blocks_for(d.Np, kTPB), kTPB, 0, st>>>(d, ptrs(M, 10), dst_dev, 10);
   return cudaGetLastError();
 }
 

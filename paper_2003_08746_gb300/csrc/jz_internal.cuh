@@ -130,6 +130,8 @@ cudaError_t pad_coordinates(const Dims& d, const double* xyz_real, const double*
 cudaError_t compute_metrics(const Dims& d, GridDev& g, double* scratch9[9], cudaStream_t st);
 // ghost fill of nvar padded fields by the state's ghost map
 cudaError_t ghost_fill(const Dims& d, double* const* f, int nvar, cudaStream_t st);
+// FP32 copy of the metrics S (9) and V; dst_dev is a device array of 10 pointers
+cudaError_t metrics_to_f32(const Dims& d, const GridDev& g, float* const* dst_dev, cudaStream_t st);
 // copy between unpadded [nvar][N] and padded real region
 cudaError_t pack_real(const Dims& d, double* const* padded, const double* flat, int nvar,
                       cudaStream_t st);
@@ -145,6 +147,10 @@ cudaError_t faces64(const Dims& d, const Consts& c, const Work64& w, const State
 cudaError_t update64(const Dims& d, const GridDev& g, const Work64& w, const State& qin, const State& qn,
                      const State& qout, const Scalars* sc, double alpha, int want_res, double* rhs_flat,
                      cudaStream_t st);
+// FP32-flux stage (one fused kernel); Sf = FP32 metrics S (9) and V.
+cudaError_t fused32(const Dims& d, const Consts& c, float* const* Sf, const State& qin, const State& qn,
+                    const State& qout, Scalars* sc, double alpha, int want_res, int want_rate, double* rhs_flat,
+                    int kchunk, cudaStream_t st);
 // boundary conditions (jet), in this order after every stage
 cudaError_t bc_farfield(const Dims& d, const Consts& c, const GridDev& g, const State& q, cudaStream_t st);
 cudaError_t bc_inout(const Dims& d, const Consts& c, const Inflow& in, const State& q, const Scalars* sc,

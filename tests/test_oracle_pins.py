@@ -492,3 +492,52 @@ def test_jet_azimuthal_equivariance():
     R = O.residual(grid, Q, c)
     Rr = O.residual(grid, rot(Q), c)
     assert torch.allclose(Rr, rot(R), rtol=0, atol=1e-12 * R.abs().max().item())
+
+
+# ---------------------------------------------------------------------------
+# c-P10  observer functional and its reverse sweep
+# ---------------------------------------------------------------------------
+def test_observer_weights_and_interpolation():
+    """Weights sum to the lateral area 2 pi r L of the observer cylinder; a pressure field
+    linear in r is interpolated exactly, so J of one state has a closed form."""
+    g = W.jet_grid(20, 24, 8)
+    grid = _grid(g)
+    obs = O.Observer(grid, 1.3)
+    L = g.xyz[0].max() - g.xyz[0].min()
+    assert abs(obs.w.sum().item() * g.nk - 2 * math.pi * 1.3 * L) < 1e-10     # w_ik is the same for every k
+    r = np.sqrt(g.xyz[1] ** 2 + g.xyz[2] ** 2)
+    one = np.ones_like(r)
+    p = 1 / GAMMA + 1e-3 * (r - 1.0)
+    q = torch.from_numpy(W.conserved(one, 0 * one, 0 * one, 0 * one, p))
+    c = O.Consts(W.jet_params())
+    J = obs.value(q, c).item()
+    expect = (1e-3 * 0.3) ** 2 * 2 * math.pi * 1.3 * L
+    assert abs(J - expect) < 1e-9 * expect
+
+
+def test_functional_reverse_sweep_matches_central_differences():
+    """dJ/dA from the reverse sweep of the discrete forward map equals central finite
+    differences (h = 1e-6) of J, component by component and along a random direction,
+    within 1e-6 of the gradient's largest component."""
+    g = W.jet_grid(20, 16, 8)
+    prm = W.jet_params(seed=4)
+    grid, c = _grid(g), O.Consts(prm)
+    q = torch.from_numpy(W.jet_state(g))
+    obs = O.Observer(grid, 0.75)
+    dt = O.cfl_dt(grid, q, c).item()
+    A = torch.as_tensor(prm.forcing_amp)
+    J, gr = O.functional_gradient(grid, q, c, A, 4, dt, obs)
+    h = 1e-6
+    rng = np.random.Generator(np.random.PCG64(8))
+    dirs = [("comp", (0, 0)), ("comp", (2, 3)), ("dir", torch.as_tensor(rng.standard_normal((8, 4))))]
+    for kind, v in dirs:
+        if kind == "comp":
+            d = torch.zeros_like(A)
+            d[v] = 1.0
+        else:
+            d = v / v.norm()
+        Jp = O.functional(grid, q, c, A + h * d, 4, dt, obs).item()
+        Jm = O.functional(grid, q, c, A - h * d, 4, dt, obs).item()
+        fd = (Jp - Jm) / (2 * h)
+        ad = (gr * d).sum().item()
+        assert abs(fd - ad) <= 1e-6 * gr.abs().max().item(), (kind, fd, ad)
