@@ -157,6 +157,26 @@ int jz_residual(jz_solver* s, const double* q, double* rhs);
  * non-positive density or pressure. */
 int jz_rk_step(jz_solver* s, int nsteps, jz_step_stats* out);
 
+/* Gradient of an observer functional with respect to the entrance-forcing
+ * amplitudes by the discrete adjoint of the time stepping (FP64 form, jet
+ * grid).  Starting from the solver's current state Q^0 at time t0, with the
+ * forcing amplitudes forcing_amps [8 modes][4 frequencies] (host; phases and
+ * Strouhal numbers from jz_params) and a time step frozen at the CFL step of
+ * Q^0 (or dt_fixed),
+ *   J = sum_{n=1..nsteps} dt sum_{i,k} w_ik (p~_ik(Q^n) - p_inf)^2,
+ * p~ the pressure on the cylinder r = r_obs (linear in r between the
+ * bracketing grid lines), w_ik = r_obs dtheta dx_i (trapezoid in x).
+ * The forward sweep stores Q^n every ckpt_every steps; the reverse sweep
+ * recomputes each checkpoint segment and each step's five stage states and
+ * runs the transposed stage, boundary-condition and ghost-fill kernels.
+ * Writes J (*J_out, host) and dJ/dA (grad_out [32], host).  The solver's
+ * state and parameters are unchanged on return; device memory for the
+ * checkpoints and adjoint arrays is allocated for the call.
+ * Errors: JZ_ERR_ARG (FP32-flux solver, periodic grid, r_obs outside the
+ * grid, bad counts), JZ_ERR_STATE (no state), JZ_ERR_OOM, JZ_ERR_CUDA. */
+int jz_adjoint_step(jz_solver* s, const double* forcing_amps, int nsteps, int ckpt_every, double r_obs,
+                    double* J_out, double* grad_out);
+
 /* ---- kernel timing ---------------------------------------------------- *
  * Kernel kinds of the stage (index of the arrays below). */
 #define JZ_PROF_NODAL    0   /* FP64 nodal pass: primitives, spectral radii, inviscid fluxes */

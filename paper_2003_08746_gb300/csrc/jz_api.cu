@@ -1,5 +1,6 @@
 // C ABI entry points (include/jz.h): handles, device memory, and the order of
 // the kernels in a time step (Algorithm 2 main loop).
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -206,6 +207,42 @@ int run_step(jz_solver* s) {
   return JZ_OK;
 }
 
+// ---- discrete adjoint: forward stages from an explicit Q^n --------------------------
+int fwd_stage(jz_solver* s, const jz::State& in, const jz::State& qn, const jz::State& out, int l) {
+  const jz::Dims& d = s->grid->d;
+  const jz::GridDev& g = s->grid->g;
+  JZ_RUN(JZ_PROF_NODAL, jz::nodal64(d, s->c, g, s->w, in, s->st));
+  JZ_RUN(JZ_PROF_VISCOUS, jz::viscous64(d, s->c, g, s->w, in, s->st));
+  JZ_RUN(JZ_PROF_FACES, jz::faces64(d, s->c, s->w, in, s->st));
+  JZ_RUN(JZ_PROF_UPDATE, jz::update64(d, g, s->w, in, qn, out, s->sc, kAlpha[l], 0, nullptr, s->st));
+  if (d.topo == JZ_TOPO_JET) {
+    JZ_RUN(JZ_PROF_BC, jz::bc_farfield(d, s->c, g, out, s->st));
+    JZ_RUN(JZ_PROF_BC, jz::bc_inout(d, s->c, s->in, out, s->sc, kAlpha[l], s->st));
+    JZ_RUN(JZ_PROF_BC, jz::bc_axis(d, out, s->st));
+  }
+  JZ_RUN(JZ_PROF_GHOST, jz::ghost_fill(d, out.q, 5, s->st));
+  return JZ_OK;
+}
+
+// One time step in -> out (in, out distinct from the solver's stage buffers).
+int fwd_step(jz_solver* s, const jz::State& in, const jz::State& out, double t, double dt) {
+  JZ_CK(jz::set_time(s->sc, t, dt, s->st));
+  const jz::State* src = &in;
+  for (int l = 0; l < 5; ++l) {
+    const jz::State& dst = l == 4 ? out : ((l % 2 == 0) ? s->qa : s->qb);
+    int r = fwd_stage(s, *src, in, dst, l);
+    if (r) return r;
+    src = &dst;
+  }
+  return JZ_OK;
+}
+
+int copy_state(jz_solver* s, const jz::State& dst, const jz::State& src) {
+  const size_t bytes = sizeof(double) * s->grid->d.Np;
+  for (int m = 0; m < 5; ++m) JZ_CK(cudaMemcpyAsync(dst.q[m], src.q[m], bytes, cudaMemcpyDeviceToDevice, s->st));
+  return JZ_OK;
+}
+
 }  // namespace
 
 namespace jz {
@@ -368,7 +405,8 @@ int jz_create(jz_grid* g, const jz_params* p, void* stream, jz_solver** out) {
     A(tmp, 10);
     Sf_dev = reinterpret_cast<float**>(tmp);
     // CTAs of 30 x 8 columns; split k so that the grid covers the SMs evenly
-    const long long tiles = (long long)((d.ni + 29) / 30) * ((d.nj + 7) / 8);
+    const int tx = jz::fused32_tile_x(), ty = jz::fused32_tile_y();
+    const long long tiles = (long long)((d.ni + tx - 1) / tx) * ((d.nj + ty - 1) / ty);
     int nch = 1;
     while (tiles * nch < 8 * 304 && nch < d.nk / 16) nch *= 2;
     s->kchunk = (d.nk + nch - 1) / nch;
@@ -512,6 +550,146 @@ int jz_rk_step(jz_solver* s, int nsteps, jz_step_stats* out) {
   out->min_p = h.min_p;
   out->steps = s->steps;
   if (h.nonfinite) return fail(JZ_ERR_NONFINITE, "state holds NaN/Inf or non-positive density/pressure");
+  return JZ_OK;
+}
+
+int jz_adjoint_step(jz_solver* s, const double* forcing_amps, int nsteps, int ckpt_every, double r_obs,
+                    double* J_out, double* grad_out) {
+  if (!s || !forcing_amps || !J_out || !grad_out) return fail(JZ_ERR_ARG, "jz_adjoint_step: NULL argument");
+  if (nsteps < 1 || ckpt_every < 1) return fail(JZ_ERR_ARG, "jz_adjoint_step: nsteps and ckpt_every must be >= 1");
+  if (s->fp32) return fail(JZ_ERR_ARG, "jz_adjoint_step: the adjoint is available for the FP64 form");
+  const jz::Dims& d = s->grid->d;
+  const jz::GridDev& g = s->grid->g;
+  if (d.topo != JZ_TOPO_JET) return fail(JZ_ERR_ARG, "jz_adjoint_step: the observer functional needs a jet grid");
+  if (!s->has_state) return fail(JZ_ERR_STATE, "jz_adjoint_step: no state set");
+  if (!(r_obs > 0.0)) return fail(JZ_ERR_ARG, "jz_adjoint_step: r_obs must be > 0");
+  // observer geometry from the node coordinates: r_j at (i = 0, k = 0), x_i at (j = 0, k = 0)
+  std::vector<double> y(d.nj), z(d.nj), x(d.ni);
+  const size_t pitch = sizeof(double) * d.Pi;
+  JZ_CK(cudaMemcpy2D(y.data(), sizeof(double), g.xyz[1] + jz::pidx(d, 0, 0, 0), pitch, sizeof(double), d.nj,
+                     cudaMemcpyDeviceToHost));
+  JZ_CK(cudaMemcpy2D(z.data(), sizeof(double), g.xyz[2] + jz::pidx(d, 0, 0, 0), pitch, sizeof(double), d.nj,
+                     cudaMemcpyDeviceToHost));
+  JZ_CK(cudaMemcpy(x.data(), g.xyz[0] + jz::pidx(d, 0, 0, 0), sizeof(double) * d.ni, cudaMemcpyDeviceToHost));
+  int j0 = -1;
+  std::vector<double> rj(d.nj);
+  for (int j = 0; j < d.nj; ++j) {
+    rj[j] = std::sqrt(y[j] * y[j] + z[j] * z[j]);
+    if (rj[j] <= r_obs) j0 = j;
+  }
+  if (j0 < 0 || j0 >= d.nj - 1) return fail(JZ_ERR_ARG, "jz_adjoint_step: r_obs = %g outside the grid", r_obs);
+  const double beta = (r_obs - rj[j0]) / (rj[j0 + 1] - rj[j0]);
+  std::vector<double> w(d.ni);
+  const double wr = r_obs * (2.0 * 3.141592653589793 / d.nk);
+  for (int i = 0; i < d.ni; ++i) {
+    const double dx = i == 0 ? 0.5 * (x[1] - x[0])
+                             : (i == d.ni - 1 ? 0.5 * (x[d.ni - 1] - x[d.ni - 2]) : 0.5 * (x[i + 1] - x[i - 1]));
+    w[i] = wr * dx;
+  }
+  // device memory for this call
+  DevMem mem;
+  cudaError_t e = cudaSuccess;
+  auto A = [&](double*& dst, size_t n) {
+    if (e != cudaSuccess) return;
+    dst = mem.alloc(n, e);
+  };
+  auto AS = [&](jz::State& st) {
+    for (int m = 0; m < 5; ++m) A(st.q[m], d.Np);
+  };
+  const int C = ckpt_every;
+  const int nseg = (nsteps + C - 1) / C;
+  double* wdev = nullptr;
+  A(wdev, d.ni);
+  jz::Adj64 a;
+  for (int m = 0; m < 5; ++m) {
+    A(a.lam[m], d.Np); A(a.qnbar[m], d.Np); A(a.acc[m], d.Np);
+  }
+  for (int dir = 0; dir < 3; ++dir) {
+    for (int m = 0; m < 5; ++m) {
+      A(a.d1b[dir][m], d.Np); A(a.d3b[dir][m], d.Np);
+    }
+    A(a.lfh[dir], d.Np); A(a.nb0[dir], d.Np); A(a.nb1[dir], d.Np);
+    A(a.cpm[dir], d.Np); A(a.c0[dir], d.Np); A(a.ubd[dir], d.Np);
+    for (int n = 0; n < 4; ++n) A(a.G[n][dir], d.Np);
+  }
+  A(a.mub, d.Np); A(a.rhob, d.Np); A(a.abar, jz::kNF); A(a.J, 1);
+  std::vector<jz::State> ck(nseg), seg(C + 1), stg(4);
+  jz::State wa, wb;
+  for (auto& st : ck) AS(st);
+  for (auto& st : seg) AS(st);
+  for (auto& st : stg) AS(st);
+  AS(wa); AS(wb);
+  if (e != cudaSuccess) return fail(JZ_ERR_OOM, "jz_adjoint_step: device allocation failed: %s", cudaGetErrorString(e));
+  JZ_CK(cudaMemcpy(wdev, w.data(), sizeof(double) * d.ni, cudaMemcpyHostToDevice));
+  // frozen time step and start time
+  if (s->c.dt_fixed <= 0.0) JZ_RUN(JZ_PROF_REDUCE, jz::cfl_rate(d, s->c, g, s->qn, s->sc, s->st));
+  JZ_RUN(JZ_PROF_REDUCE, jz::set_dt(s->c, s->sc, 0, s->st));
+  jz::Scalars h;
+  JZ_CK(cudaMemcpyAsync(&h, s->sc, sizeof h, cudaMemcpyDeviceToHost, s->st));
+  JZ_CK(cudaStreamSynchronize(s->st));
+  const double dt = h.dt, t0 = h.t;
+  // forcing amplitudes of this evaluation (restored on return)
+  double saved[jz::kNF];
+  for (int f = 0; f < jz::kNF; ++f) {
+    saved[f] = s->in.amp[f];
+    s->in.amp[f] = forcing_amps[f];
+  }
+  struct Restore {
+    jz_solver* s;
+    double* v;
+    ~Restore() {
+      for (int f = 0; f < jz::kNF; ++f) s->in.amp[f] = v[f];
+    }
+  } restore{s, saved};
+  // forward sweep with checkpoints; J accumulated on the device
+  int r = copy_state(s, wa, s->qn);
+  if (r) return r;
+  for (int n = 0; n < nsteps; ++n) {
+    if (n % C == 0) {
+      r = copy_state(s, ck[n / C], wa);
+      if (r) return r;
+    }
+    r = fwd_step(s, wa, wb, t0 + n * dt, dt);
+    if (r) return r;
+    JZ_RUN(JZ_PROF_ADJOINT, jz::observer(d, s->c, wb, wdev, j0, beta, dt, a, 0, s->st));
+    std::swap(wa, wb);
+  }
+  // reverse sweep, one checkpoint segment at a time
+  for (int sg = nseg - 1; sg >= 0; --sg) {
+    const int n0 = sg * C, n1 = std::min(n0 + C, nsteps);
+    r = copy_state(s, seg[0], ck[sg]);
+    if (r) return r;
+    for (int q = 0; q < n1 - n0; ++q) {
+      r = fwd_step(s, seg[q], seg[q + 1], t0 + (n0 + q) * dt, dt);
+      if (r) return r;
+    }
+    for (int n = n1 - 1; n >= n0; --n) {
+      const jz::State& Qn = seg[n - n0];
+      const jz::State& Qn1 = seg[n - n0 + 1];
+      const double tn = t0 + n * dt;
+      JZ_RUN(JZ_PROF_ADJOINT, jz::observer(d, s->c, Qn1, wdev, j0, beta, dt, a, 1, s->st));
+      // stage states of step n
+      JZ_CK(jz::set_time(s->sc, tn, dt, s->st));
+      const jz::State* st[6] = {&Qn, &stg[0], &stg[1], &stg[2], &stg[3], &Qn1};
+      for (int l = 0; l < 4; ++l) {
+        r = fwd_stage(s, *st[l], Qn, *st[l + 1], l);
+        if (r) return r;
+      }
+      for (int l = 4; l >= 0; --l) {
+        JZ_RUN(JZ_PROF_ADJOINT, jz::adj_bcs(d, s->c, g, s->in, *st[l + 1], a, tn + kAlpha[l] * dt, s->st));
+        JZ_RUN(JZ_PROF_ADJOINT, jz::adj_update(d, g, a, kAlpha[l] * dt, s->st));
+        JZ_RUN(JZ_PROF_NODAL, jz::nodal64(d, s->c, g, s->w, *st[l], s->st));
+        JZ_RUN(JZ_PROF_VISCOUS, jz::viscous64(d, s->c, g, s->w, *st[l], s->st));
+        JZ_RUN(JZ_PROF_ADJOINT, jz::adj_stage(d, s->c, g, s->w, *st[l], a, s->st));
+      }
+      JZ_RUN(JZ_PROF_ADJOINT, jz::adj_add_qn(d, a, s->st));
+    }
+  }
+  double Jh = 0.0;
+  JZ_CK(cudaMemcpyAsync(&Jh, a.J, sizeof(double), cudaMemcpyDeviceToHost, s->st));
+  JZ_CK(cudaMemcpyAsync(grad_out, a.abar, sizeof(double) * jz::kNF, cudaMemcpyDeviceToHost, s->st));
+  JZ_CK(cudaStreamSynchronize(s->st));
+  *J_out = Jh;
   return JZ_OK;
 }
 

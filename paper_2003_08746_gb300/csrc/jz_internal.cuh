@@ -113,6 +113,26 @@ struct State {
   double* q[5];
 };
 
+// Adjoint arrays (each Np elements unless noted).
+struct Adj64 {
+  double* lam[5];          // running adjoint of the stage state (real nodes; P0 as scratch)
+  double* qnbar[5];        // adjoint of Q^n collected over the stages of a step
+  double* acc[5];          // -(alpha dt / V) lam on advanced nodes, 0 elsewhere
+  double* d1b[3][5];       // face adjoints: d(out)/d(Q_{n+1} - Q_n)
+  double* d3b[3][5];       //               d(out)/d(third difference)
+  double* lfh[3];          // half the adjoint of the face spectral radius
+  double* nb0[3];          // sensor adjoint sent to node n of face n+1/2
+  double* nb1[3];          // ... and to node n+1
+  double* G[4][3];         // adjoint of delta_dir f, f = u, v, w, T
+  double* cpm[3];          // sensor adjoint coefficient of p_{n+1} and p_{n-1}
+  double* c0[3];           // ... of p_n
+  double* ubd[3];          // direct adjoint of u_i from the viscous energy flux
+  double* mub;             // adjoint of the Sutherland viscosity
+  double* rhob;            // direct adjoint of rho (eddy viscosity)
+  double* abar;            // [32] dJ/dA accumulator
+  double* J;               // [1] functional accumulator
+};
+
 // Inflow tables (jet): base profile u0[nk][nj] and forcing shapes
 // Gf[m*4+f][nk][nj] = g(r) cos(m theta + phi_mf), at i = 0.
 struct Inflow {
@@ -151,6 +171,8 @@ cudaError_t update64(const Dims& d, const GridDev& g, const Work64& w, const Sta
 cudaError_t fused32(const Dims& d, const Consts& c, float* const* Sf, const State& qin, const State& qn,
                     const State& qout, Scalars* sc, double alpha, int want_res, int want_rate, double* rhs_flat,
                     int kchunk, cudaStream_t st);
+int fused32_tile_x();
+int fused32_tile_y();
 // boundary conditions (jet), in this order after every stage
 cudaError_t bc_farfield(const Dims& d, const Consts& c, const GridDev& g, const State& q, cudaStream_t st);
 cudaError_t bc_inout(const Dims& d, const Consts& c, const Inflow& in, const State& q, const Scalars* sc,
@@ -166,6 +188,17 @@ int stat_partial_count();
 cudaError_t stats_with(const Dims& d, const Consts& c, const GridDev& g, const State& q, Scalars* sc,
                        double* part, cudaStream_t st);
 cudaError_t check_volume(const Dims& d, const GridDev& g, int* bad, cudaStream_t st);
+
+// adjoint (jz_adjoint.cu)
+cudaError_t adj_update(const Dims& d, const GridDev& g, const Adj64& a, double adt, cudaStream_t st);
+cudaError_t adj_stage(const Dims& d, const Consts& c, const GridDev& g, const Work64& w, const State& q,
+                      const Adj64& a, cudaStream_t st);
+cudaError_t adj_add_qn(const Dims& d, const Adj64& a, cudaStream_t st);
+cudaError_t adj_bcs(const Dims& d, const Consts& c, const GridDev& g, const Inflow& in, const State& q,
+                    const Adj64& a, double ts, cudaStream_t st);
+cudaError_t observer(const Dims& d, const Consts& c, const State& q, const double* w, int j0, double beta,
+                     double dt, const Adj64& a, int want_grad, cudaStream_t st);
+cudaError_t set_time(Scalars* sc, double t, double dt, cudaStream_t st);
 
 // ---- shared with the C ABI layer ------------------------------------------
 // Record an error message for jz_last_error(); returns code.

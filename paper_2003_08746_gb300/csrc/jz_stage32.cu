@@ -27,7 +27,13 @@
 namespace jz {
 namespace {
 
-constexpr int TX = 30, TY = 8;
+#ifndef JZ_FUSED_TX
+#define JZ_FUSED_TX 30
+#endif
+#ifndef JZ_FUSED_TY
+#define JZ_FUSED_TY 8
+#endif
+constexpr int TX = JZ_FUSED_TX, TY = JZ_FUSED_TY;
 constexpr int H1X = TX + 2, H1Y = TY + 2, NP1 = H1X * H1Y;   // 32 x 10
 constexpr int H2X = TX + 4, H2Y = TY + 4, NP2 = H2X * H2Y;   // 34 x 12
 constexpr int NT = NP1;                                      // threads per CTA
@@ -69,8 +75,30 @@ __device__ __forceinline__ double f32_to_f64(float f) {
   return __hiloint2double((int)(s | (e11 << 20) | (m >> 3)), (int)(m << 29));
 }
 
+// Single MUFU approximations (relative error ~2^-22), far inside the FP32-flux
+// form's error budget.
+__device__ __forceinline__ float f_rcp(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ float f_sqrt(float x) {
+  float r;
+  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ float f_ex2(float x) {
+  float r;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ float f_lg2(float x) {
+  float r;
+  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
 __device__ __forceinline__ float cbrt_pos(float x) {   // x >= 0; 0 -> 0
-  return x > 0.f ? exp2f(log2f(x) * (1.f / 3.f)) : 0.f;
+  return x > 0.f ? f_ex2(f_lg2(x) * (1.f / 3.f)) : 0.f;
 }
 
 __device__ __forceinline__ int ring3(int k) { return (k + 6) % 3; }   // k >= -6
@@ -109,20 +137,27 @@ struct Args {
   int want_rate;
 };
 
-// Load the FP64 state of plane k at this thread's halo-2 points into registers.
-__device__ __forceinline__ void prefetch(const Args& A, int i0, int j0, int k, double reg[NLOAD][5]) {
+// Padded index at k = 0 of this thread's halo-2 load points (-1: outside the padded box).
+__device__ __forceinline__ void load_bases(const Args& A, int i0, int j0, long long base[NLOAD]) {
 #pragma unroll
   for (int r = 0; r < NLOAD; ++r) {
     const int t = threadIdx.x + r * NT;
-    if (t < NP2) {
-      const int i = i0 - 2 + t % H2X, j = j0 - 2 + t / H2X;
-      if (in_padded(A.d, i, j)) {
-        const long long p = pidx(A.d, i, j, k);
+    const int i = i0 - 2 + t % H2X, j = j0 - 2 + t / H2X;
+    base[r] = (t < NP2 && in_padded(A.d, i, j)) ? pidx(A.d, i, j, 0) : -1;
+  }
+}
+
+// Load the FP64 state of plane k at this thread's halo-2 points into registers.
+__device__ __forceinline__ void prefetch(const Args& A, const long long base[NLOAD], int k, double reg[NLOAD][5]) {
+  const long long koff = (long long)k * A.d.sk;
 #pragma unroll
-        for (int m = 0; m < 5; ++m) reg[r][m] = __ldg(A.qin[m] + p);
-      } else {
-        reg[r][0] = 1.0; reg[r][1] = 0.0; reg[r][2] = 0.0; reg[r][3] = 0.0; reg[r][4] = A.c.e_inf;
-      }
+  for (int r = 0; r < NLOAD; ++r) {
+    if (base[r] >= 0) {
+      const long long p = base[r] + koff;
+#pragma unroll
+      for (int m = 0; m < 5; ++m) reg[r][m] = __ldg(A.qin[m] + p);
+    } else {
+      reg[r][0] = 1.0; reg[r][1] = 0.0; reg[r][2] = 0.0; reg[r][3] = 0.0; reg[r][4] = A.c.e_inf;
     }
   }
 }
@@ -138,7 +173,7 @@ __device__ __forceinline__ void store_prims(const Args& A, Smem& sm, int slot, c
       const float m1 = f64_to_f32(reg[r][1]), m2 = f64_to_f32(reg[r][2]), m3 = f64_to_f32(reg[r][3]);
       const float ep = f64_to_f32(reg[r][4] - c.e_inf);
       const float rho = rp + 1.f;
-      const float ir = 1.f / rho;
+      const float ir = f_rcp(rho);
       const float u = m1 * ir, v = m2 * ir, w = m3 * ir;
       const float pp = c.gm1 * (ep - 0.5f * (m1 * u + m2 * v + m3 * w));
       const float T = c.gamma * (pp + c.p_inf) * ir;
@@ -157,28 +192,38 @@ __device__ __forceinline__ void store_prims(const Args& A, Smem& sm, int slot, c
   }
 }
 
+// Metrics S (9) and V of this thread's halo-1 node of plane q (nb < 0: outside).
+__device__ __forceinline__ void load_metrics(const Args& A, long long nb, int q, float met[10]) {
+  if (nb < 0) {
+#pragma unroll
+    for (int f = 0; f < 10; ++f) met[f] = 0.f;
+    return;
+  }
+  const long long p = nb + (long long)q * A.d.sk;
+#pragma unroll
+  for (int f = 0; f < 10; ++f) met[f] = __ldg(A.S[f] + p);
+}
+
 // Nodal fluxes, spectral radii and sensors of one node of plane q (slots
-// sm_, s0, sp of planes q-1, q, q+1) at halo-1 index t.
-__device__ void nodal(const Args& A, Smem& sm, int i0, int j0, int q, int s_m, int s_0, int s_p, int g) {
+// s_m, s_0, s_p of planes q-1, q, q+1) at halo-1 index t.
+__device__ void nodal(const Args& A, Smem& sm, long long nb, const float met[10], int s_m, int s_0, int s_p, int g) {
   const ConstsF& c = A.c;
   const int t = threadIdx.x;
   const int x1 = t % H1X, y1 = t / H1X;
-  const int i = i0 - 1 + x1, j = j0 - 1 + y1;
   const int c2 = (y1 + 1) * H2X + (x1 + 1);
   float* Fo = &sm.flux[g][0][0];
-  if (!in_padded(A.d, i, j)) {
+  if (nb < 0) {
 #pragma unroll 1
     for (int f = 0; f < NGF; ++f) Fo[f * NP1 + t] = 0.f;
     return;
   }
-  const long long p = pidx(A.d, i, j, q);
   float S[3][3];
 #pragma unroll
   for (int dir = 0; dir < 3; ++dir)
 #pragma unroll
-    for (int cc = 0; cc < 3; ++cc) S[dir][cc] = __ldg(A.S[3 * dir + cc] + p);
-  const float V = __ldg(A.S[9] + p);
-  const float iV = V > 0.f ? 1.f / V : 0.f;
+    for (int cc = 0; cc < 3; ++cc) S[dir][cc] = met[3 * dir + cc];
+  const float V = met[9];
+  const float iV = V > 0.f ? f_rcp(V) : 0.f;
   const float* P0 = &sm.prim[s_0][0][0];
   const float* Pm = &sm.prim[s_m][0][0];
   const float* Pp = &sm.prim[s_p][0][0];
@@ -198,8 +243,8 @@ __device__ void nodal(const Args& A, Smem& sm, int i0, int j0, int q, int s_m, i
   const float u = P0[F_U * NP2 + c2], v = P0[F_V * NP2 + c2], w = P0[F_W * NP2 + c2];
   const float T = P0[F_T * NP2 + c2], pp = P0[F_P * NP2 + c2];
   const float ep = P0[F_E * NP2 + c2];
-  const float a = sqrtf(T);
-  const float mu = c.mu_ref * (T * a) * c.sut_num / (T + c.S_hat);
+  const float a = f_sqrt(T);
+  const float mu = c.mu_ref * (T * a) * c.sut_num * f_rcp(T + c.S_hat);
   float Sij[3][3];
 #pragma unroll
   for (int x = 0; x < 3; ++x)
@@ -211,7 +256,7 @@ __device__ void nodal(const Args& A, Smem& sm, int i0, int j0, int q, int s_m, i
   for (int x = 0; x < 3; ++x)
 #pragma unroll
     for (int y = 0; y < 3; ++y) SS += Sij[x][y] * Sij[x][y];
-  const float Smod = sqrtf(2.f * SS);
+  const float Smod = f_sqrt(2.f * SS);
   const float csd = c.C_s * cbrt_pos(V);
   const float mu_sgs = rho * (csd * csd) * Smod;
   const float mu_eff = mu + mu_sgs;
@@ -235,7 +280,7 @@ __device__ void nodal(const Args& A, Smem& sm, int i0, int j0, int q, int s_m, i
 #pragma unroll
   for (int dir = 0; dir < 3; ++dir) {
     const float U = S[dir][0] * u + S[dir][1] * v + S[dir][2] * w;
-    const float smag = sqrtf(S[dir][0] * S[dir][0] + S[dir][1] * S[dir][1] + S[dir][2] * S[dir][2]);
+    const float smag = f_sqrt(S[dir][0] * S[dir][0] + S[dir][1] * S[dir][1] + S[dir][2] * S[dir][2]);
     lam[dir] = fabsf(U) + a * smag;
     const int gh = G_HX + 5 * dir;
     Fo[(gh + 0) * NP1 + t] = rho * U;
@@ -257,9 +302,9 @@ __device__ void nodal(const Args& A, Smem& sm, int i0, int j0, int q, int s_m, i
   const float pxm = pr0[c2 - 1], pxp = pr0[c2 + 1], pym = pr0[c2 - H2X], pyp = pr0[c2 + H2X];
   const float pzm = Pm[F_P * NP2 + c2], pzp = Pp[F_P * NP2 + c2];
   const float p4 = 4.f * c.p_inf;
-  Fo[(G_N + 0) * NP1 + t] = fabsf(pxp - 2.f * pp + pxm) / (pxp + 2.f * pp + pxm + p4);
-  Fo[(G_N + 1) * NP1 + t] = fabsf(pyp - 2.f * pp + pym) / (pyp + 2.f * pp + pym + p4);
-  Fo[(G_N + 2) * NP1 + t] = fabsf(pzp - 2.f * pp + pzm) / (pzp + 2.f * pp + pzm + p4);
+  Fo[(G_N + 0) * NP1 + t] = fabsf(pxp - 2.f * pp + pxm) * f_rcp(pxp + 2.f * pp + pxm + p4);
+  Fo[(G_N + 1) * NP1 + t] = fabsf(pyp - 2.f * pp + pym) * f_rcp(pyp + 2.f * pp + pym + p4);
+  Fo[(G_N + 2) * NP1 + t] = fabsf(pzp - 2.f * pp + pzm) * f_rcp(pzp + 2.f * pp + pzm + p4);
   Fo[G_IV * NP1 + t] = iV;
 }
 
@@ -268,7 +313,9 @@ __device__ __forceinline__ void load_q(const float* P, int c2, float q[5]) {
   for (int m = 0; m < 5; ++m) q[m] = P[m * NP2 + c2];
 }
 
-__global__ void __launch_bounds__(NT, 2) k_fused32(Args A) {
+constexpr int kMinBlocks = NT <= 320 ? 2 : 1;
+
+__global__ void __launch_bounds__(NT, kMinBlocks) k_fused32(Args A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Smem& sm = *reinterpret_cast<Smem*>(smem_raw);
   const Dims& d = A.d;
@@ -285,13 +332,21 @@ __global__ void __launch_bounds__(NT, 2) k_fused32(Args A) {
   const int c1 = (oy + 1) * H1X + (ox + 1);
   const int c2 = (oy + 2) * H2X + (ox + 2);
 
+  long long lb[NLOAD];
+  load_bases(A, i0, j0, lb);
+  long long nb;                                    // halo-1 node of this thread (nodal work)
+  {
+    const int i = i0 - 1 + t % H1X, j = j0 - 1 + t / H1X;
+    nb = in_padded(d, i, j) ? pidx(d, i, j, 0) : -1;
+  }
+  const long long ob = outv ? pidx(d, oi, oj, 0) : 0;   // output node
   double reg[NLOAD][5];
   // prime: planes k0-2, k0-1 into the ring, plane k0 into registers
-  prefetch(A, i0, j0, k0 - 2, reg);
+  prefetch(A, lb, k0 - 2, reg);
   store_prims(A, sm, ring3(k0 - 2), reg);
-  prefetch(A, i0, j0, k0 - 1, reg);
+  prefetch(A, lb, k0 - 1, reg);
   store_prims(A, sm, ring3(k0 - 1), reg);
-  prefetch(A, i0, j0, k0, reg);
+  prefetch(A, lb, k0, reg);
 
   float Hz_prev[5] = {0, 0, 0, 0, 0};   // H^zeta(p-1)
   float Dz_prev[5] = {0, 0, 0, 0, 0};   // d^zeta(p-1/2)
@@ -301,12 +356,14 @@ __global__ void __launch_bounds__(NT, 2) k_fused32(Args A) {
   float res = 0.f, rate = 0.f;
 
   for (int p = k0 - 2; p < k1; ++p) {
-    // (a) plane p+2 -> ring; prefetch plane p+3
+    // (a) metrics of plane p+1 (used in (b)); plane p+2 -> ring; prefetch plane p+3
+    float met[10];
+    load_metrics(A, nb, p + 1, met);
     store_prims(A, sm, ring3(p + 2), reg);
-    if (p + 3 <= k1 + 1) prefetch(A, i0, j0, p + 3, reg);
+    if (p + 3 <= k1 + 1) prefetch(A, lb, p + 3, reg);
     __syncthreads();
     // (b) nodal quantities of plane p+1
-    nodal(A, sm, i0, j0, p + 1, ring3(p), ring3(p + 1), ring3(p + 2), (p + 1) & 1);
+    nodal(A, sm, nb, met, ring3(p), ring3(p + 1), ring3(p + 2), (p + 1) & 1);
     __syncthreads();
     // (c) zeta face p+1/2 and the output plane p
     if (outth) {
@@ -344,7 +401,7 @@ __global__ void __launch_bounds__(NT, 2) k_fused32(Args A) {
           acc += 0.5f * (Fp1[(G_HZ + m) * NP1 + c1] - Hz_prev[m]) - (Dz[m] - Dz_prev[m]);
           R[m] = acc * iV;
         }
-        const long long pp = pidx(d, oi, oj, p);
+        const long long pp = ob + (long long)p * d.sk;
         if (A.rhs) {
           const long long N = (long long)d.ni * d.nj * d.nk;
           const long long ridx = ((long long)p * d.nj + oj) * d.ni + oi;
@@ -359,17 +416,17 @@ __global__ void __launch_bounds__(NT, 2) k_fused32(Args A) {
           }
           if (A.want_rate) {
             const float rho = f64_to_f32(qnew[0]);
-            const float ir = 1.f / rho;
+            const float ir = f_rcp(rho);
             const float m1 = f64_to_f32(qnew[1]), m2 = f64_to_f32(qnew[2]), m3 = f64_to_f32(qnew[3]);
             const float u = m1 * ir, v = m2 * ir, w = m3 * ir;
             const float pr = c.gm1 * (f64_to_f32(qnew[4] - c.e_inf) - 0.5f * (m1 * u + m2 * v + m3 * w)) + c.p_inf;
-            const float a = sqrtf(c.gamma * pr * ir);
+            const float a = f_sqrt(c.gamma * pr * ir);
             float ls = 0.f;
 #pragma unroll
             for (int dir = 0; dir < 3; ++dir) {
               const float sx = __ldg(A.S[3 * dir] + pp), sy = __ldg(A.S[3 * dir + 1] + pp),
                           sz = __ldg(A.S[3 * dir + 2] + pp);
-              ls += fabsf(sx * u + sy * v + sz * w) + a * sqrtf(sx * sx + sy * sy + sz * sz);
+              ls += fabsf(sx * u + sy * v + sz * w) + a * f_sqrt(sx * sx + sy * sy + sz * sz);
             }
             rate = fmaxf(rate, ls * iV);
           }

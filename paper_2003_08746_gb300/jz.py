@@ -26,7 +26,8 @@ N_MODES, N_FREQ = 8, 4
 # Entry points declared in include/jz.h (checked by the tests).
 EXPORTS = ("jz_last_error", "jz_version", "jz_create_grid", "jz_destroy_grid", "jz_compute_metrics",
            "jz_get_metrics", "jz_create", "jz_destroy", "jz_set_state", "jz_get_state", "jz_residual",
-           "jz_rk_step", "jz_profile", "jz_profile_read", "jz_profile_name", "jz_residual_noalloc")
+           "jz_rk_step", "jz_profile", "jz_profile_read", "jz_profile_name", "jz_residual_noalloc",
+           "jz_adjoint_step")
 JZ_NOALLOC_SCRATCH_BYTES = 64 * 1024 * 1024
 JZ_NPROF = 9
 
@@ -84,6 +85,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
         "jz_profile_read": ([vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong)], i),
         "jz_profile_name": ([i], ctypes.c_char_p),
         "jz_residual_noalloc": ([vp, ctypes.POINTER(jz_params), vp, vp, vp], i),
+        "jz_adjoint_step": ([vp, vp, i, i, d, ctypes.POINTER(ctypes.c_double), vp], i),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -184,6 +186,41 @@ def jz_rk_step(h, nsteps: int, want_stats: bool = True):
     st = jz_step_stats() if want_stats else None
     _check(load().jz_rk_step(h, int(nsteps), ctypes.byref(st) if st is not None else None))
     return st
+
+
+def jz_adjoint_step(h, amps, nsteps: int, ckpt_every: int, r_obs: float):
+    """(J, dJ/dA [8][4]) of the observer functional by the discrete adjoint (see include/jz.h)."""
+    a = np.ascontiguousarray(np.asarray(amps, dtype=np.float64).reshape(N_MODES * N_FREQ))
+    J = ctypes.c_double()
+    g = np.empty(N_MODES * N_FREQ)
+    _check(load().jz_adjoint_step(h, _ptr(a), int(nsteps), int(ckpt_every), float(r_obs), ctypes.byref(J), _ptr(g)))
+    return J.value, g.reshape(N_MODES, N_FREQ)
+
+
+def _jet_functional_class():
+    import torch
+
+    class JetFunctional(torch.autograd.Function):
+        """J(A) of the observer functional as a differentiable function of the forcing
+        amplitudes A [8][4]: forward and gradient both come from jz_adjoint_step."""
+
+        @staticmethod
+        def forward(ctx, amps, solver, nsteps, ckpt_every, r_obs):
+            J, g = jz_adjoint_step(solver.h, amps.detach().cpu().numpy(), nsteps, ckpt_every, r_obs)
+            ctx.save_for_backward(torch.as_tensor(g, dtype=amps.dtype, device=amps.device))
+            return amps.new_tensor(J)
+
+        @staticmethod
+        def backward(ctx, gJ):
+            (g,) = ctx.saved_tensors
+            return gJ * g, None, None, None, None
+
+    return JetFunctional
+
+
+def jet_functional(amps, solver, nsteps: int, ckpt_every: int, r_obs: float):
+    """Differentiable J(A) (torch.autograd.Function over jz_adjoint_step)."""
+    return _jet_functional_class().apply(amps, solver, nsteps, ckpt_every, r_obs)
 
 
 def jz_profile(h, enable: bool):
