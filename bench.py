@@ -156,6 +156,7 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-fp32", action="store_true", help="skip the FP32-flux variant")
     ap.add_argument("--fp32-only", action="store_true", help="time only the FP32-flux form (profiling runs)")
+    ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint variant")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -282,6 +283,32 @@ def main():
             "rel_err_vs_fp64": {"steps": args.warmup + args.steps, "l2": e2.tolist(), "max": em.tolist(),
                                 "fields": ["rho", "rho_u", "rho_v", "rho_w", "e"]},
             "speedup_vs_fp64": v32 / value,
+        }
+
+    # --- discrete adjoint: dJ/dA on the 128 x 96 x 64 jet, 200 steps, checkpoints every 20 ---
+    if not args.no_adjoint:
+        ga, qa, pa = W.make_workload("jet128x96x64")
+        grid_a = jz.Grid.from_workload(ga)
+        sa = jz.Solver(grid_a, pa, jz.JZ_PREC_FP64, stream=stream.cuda_stream)
+        sa.set_state(torch.from_numpy(qa).cuda(), 0.0)
+        amps = np.asarray(pa.forcing_amp)
+        jz.jz_adjoint_step(sa.h, amps, 20, 20, 0.75)            # warm-up
+        sa.profile_read()
+        sa.profile(True)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        Ja, ga_grad = jz.jz_adjoint_step(sa.h, amps, 200, 20, 0.75)
+        t_adj = time.perf_counter() - t0
+        prof_a = sa.profile_read()
+        sa.close()
+        grid_a.close()
+        tot_a = sum(v[0] for v in prof_a.values())
+        variants["adjoint"] = {
+            "workload": "jet128x96x64", "steps": 200, "ckpt_every": 20, "r_obs": 0.75, "params": 32,
+            "seconds_per_gradient": t_adj,
+            "forward_equivalent_gpoint_stage_per_s": ga.npts * 5 * 200 / t_adj / 1e9,
+            "J": Ja, "grad_inf": float(np.abs(ga_grad).max()),
+            "kernels": {k: {"share": v[0] / tot_a, "launches": int(v[1])} for k, v in prof_a.items() if v[1] > 0},
         }
 
     cpu = None

@@ -84,8 +84,10 @@ def test_adjoint_jet128x96x64_200_steps(jz, r_obs):
     """The adjoint configuration: 128 x 96 x 64, 200 steps, checkpoints every 20 steps.
 
     At r = 3 the observer lies beyond the acoustic reach of the entrance forcing in 200
-    steps, so J depends on A only through the stencil's numerical tail; the check there
-    uses |g_adj - g_fd| <= 1e-6 max(|g_fd|_inf, floor).  r = 0.75 is the reachable variant.
+    steps: the pressure there differs from p_inf only at round-off (J ~ 1e-27), so J has
+    no sensitivity above round-off and both the adjoint and the finite-difference gradient
+    must be below a round-off floor (1e-20).  r = 0.75 is the reachable variant, checked
+    to 1e-6 of the gradient's largest component.
     """
     import time
     g, prm, q, grid, s = _setup(jz, (128, 96, 64))
@@ -98,9 +100,11 @@ def test_adjoint_jet128x96x64_200_steps(jz, r_obs):
     d /= np.linalg.norm(d)
     fd = _fd(jz, s, A, d, 200, 200, r_obs)
     ad = float((gr * d).sum())
-    floor = 1e-12 * max(J, 1e-30)
     print(f"r_obs={r_obs}: J={J:.6e} |g|inf={np.abs(gr).max():.3e} fd={fd:.6e} ad={ad:.6e} adjoint {t_adj:.2f} s")
-    assert abs(fd - ad) <= 1e-6 * max(np.abs(gr).max(), abs(fd), floor)
+    if r_obs >= 3.0:
+        assert J < 1e-20 and np.abs(gr).max() < 1e-20 and abs(fd) < 1e-20
+    else:
+        assert abs(fd - ad) <= 1e-6 * np.abs(gr).max()
 
 
 def test_jet_functional_autograd(jz):
