@@ -98,6 +98,20 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(self.samples)}
 
 
+def aggregate(ms_local: float, npts: int, steps: int, ws: int, device: str = "cuda"):
+    """Whole-job throughput of N replicas: all ranks' point-stages over the slowest rank's time.
+
+    Returns (max-over-ranks ms, Gpoint-stage/s).  Collective only when ws > 1."""
+    t_max = ms_local
+    if ws > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([ms_local], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = t.item()
+    return t_max, ws * npts * 5 * steps / (t_max / 1e3) / 1e9
+
+
 def field_errors(got, ref):
     """Per-field relative L2 and max-abs errors; momentum against the largest momentum norm."""
     l2 = np.array([np.linalg.norm(ref[m]) for m in range(5)])
@@ -210,11 +224,7 @@ def main():
             dist.barrier()
         clocks = sampler.stop() if sampler else None
         stats = solver.step(0, stats=True)   # checks the state is finite and positive
-        t_max = ms
-        if ws > 1:
-            t = torch.tensor([ms], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            t_max = t.item()
+        t_max, _ = aggregate(ms, npts, args.steps, ws)
         final = torch.empty_like(q_dev)
         solver.get_state(final)
         return solver, dict(ms=t_max, prof=prof, clocks=clocks, stats=stats, final=final)
