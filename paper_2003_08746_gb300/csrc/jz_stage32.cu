@@ -7,14 +7,16 @@
 //
 // Each CTA owns a TX x TY tile of (i, j) columns and marches in k.  Shared
 // memory holds a ring of three planes of FP32 primitives (tile + 2-node
-// halo) and a ring of two planes of nodal fluxes, spectral radii and
-// sensors (tile + 1-node halo).  Per plane:
+// halo), a ring of two planes of in-plane nodal fluxes, spectral radii and
+// sensors (tile + 1-node halo), the same for the zeta direction (tile only),
+// and the xi/eta dissipation faces of one plane.  Per plane:
 //   (a) the FP64 state of plane k+2 (prefetched into registers one plane
 //       earlier) is converted to FP32 and reduced to primitives,
 //   (b) every node of plane k+1 within one node of the tile gets its
 //       gradients, viscous and inviscid transformed fluxes H^dir, spectral
-//       radii Lambda^dir and pressure sensors nu^dir,
-//   (c) the tile of plane k gets its dissipation faces, RHS and update.
+//       radii Lambda^dir and pressure sensors nu^dir; the same threads then
+//       compute each xi and eta dissipation face of plane k once,
+//   (c) the tile of plane k gets its zeta face, RHS and update.
 //
 // On a GB300 the FP64 pipe (DADD/DFMA, and also the F2F conversions between
 // FP64 and FP32) issues ~2 instructions per SM per clock against 128 for
@@ -40,14 +42,23 @@ constexpr int NT = NP1;                                      // threads per CTA
 constexpr int NOUT = TX * TY;
 constexpr int NLOAD = (NP2 + NT - 1) / NT;                   // halo-2 points per thread
 
-// primitive ring: rho' = rho - 1, m1, m2, m3, e' = e - e_inf, u, v, w, T, p' = p - p_inf
-constexpr int F_R = 0, F_E = 4, F_U = 5, F_V = 6, F_W = 7, F_T = 8, F_P = 9, NPF = 10;
-// flux ring: H^xi(5), H^eta(5), H^zeta(5), Lambda(3), nu(3), 1/V
-constexpr int G_HX = 0, G_HY = 5, G_HZ = 10, G_L = 15, G_N = 18, G_IV = 21, NGF = 22;
+// primitive ring: rho' = rho - 1, m1, m2, m3, e' = e - e_inf, 1/rho, p' = p - p_inf
+// (u = m/rho and T = gamma p/rho are formed where they are used)
+constexpr int F_R = 0, F_E = 4, F_I = 5, F_P = 6, NPF = 7;
+constexpr int NRING = 4;           // planes k-1 .. k+2: the next plane's conversion needs no barrier
+// in-plane flux ring (tile + 1 halo): H^xi(5), H^eta(5), Lambda^xi, Lambda^eta, nu^xi, nu^eta
+constexpr int X_HX = 0, X_HY = 5, X_LX = 10, X_LY = 11, X_NX = 12, X_NY = 13, NXF = 14;
+// zeta ring (tile): H^zeta(5), Lambda^zeta, nu^zeta, 1/V
+constexpr int Z_HZ = 0, Z_L = 5, Z_N = 6, Z_IV = 7, NZF = 8;
+// xi faces: TY rows of TX+1; eta faces: TY+1 rows of TX
+constexpr int NFX = TY * (TX + 1), NFY = (TY + 1) * TX, NFACE = NFX + NFY;
 
 struct Smem {
-  float prim[3][NPF][NP2];
-  float flux[2][NGF][NP1];
+  float prim[NRING][NPF][NP2];
+  float fxy[2][NXF][NP1];
+  float fz[2][NZF][NOUT];
+  float dx[5][NFX];
+  float dy[5][NFY];
 };
 
 struct ConstsF {
@@ -97,11 +108,16 @@ __device__ __forceinline__ float f_lg2(float x) {
   asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
   return r;
 }
+// Ask L2 to fetch the sector holding p (no register, no wait).
+__device__ __forceinline__ void prefetch_l2(const void* p) {
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
 __device__ __forceinline__ float cbrt_pos(float x) {   // x >= 0; 0 -> 0
   return x > 0.f ? f_ex2(f_lg2(x) * (1.f / 3.f)) : 0.f;
 }
 
-__device__ __forceinline__ int ring3(int k) { return (k + 6) % 3; }   // k >= -6
+__device__ __forceinline__ int ring(int k) { return (k + 8) & (NRING - 1); }   // k >= -8
 
 __device__ __forceinline__ bool in_padded(const Dims& d, int i, int j) {
   return i >= -kG && i <= d.ni + 1 && j >= -kG && j <= d.nj + 1;
@@ -137,13 +153,24 @@ struct Args {
   int want_rate;
 };
 
+// Halo-2 point loaded by this thread in round r: round 0 covers points 0..NT-1;
+// round 1 goes first to the threads that have no output node (they are idle in
+// the output phase), then to the lowest threads.  -1: none.
+__device__ __forceinline__ int load_point(int r) {
+  const int t = threadIdx.x;
+  if (r == 0) return t < NP2 ? t : -1;
+  const int extra = NT - NOUT;                       // threads without an output node
+  if (t >= NOUT) return NT + (t - NOUT) < NP2 ? NT + (t - NOUT) : -1;
+  return NT + extra + t < NP2 ? NT + extra + t : -1;
+}
+
 // Padded index at k = 0 of this thread's halo-2 load points (-1: outside the padded box).
 __device__ __forceinline__ void load_bases(const Args& A, int i0, int j0, long long base[NLOAD]) {
 #pragma unroll
   for (int r = 0; r < NLOAD; ++r) {
-    const int t = threadIdx.x + r * NT;
+    const int t = load_point(r);
     const int i = i0 - 2 + t % H2X, j = j0 - 2 + t / H2X;
-    base[r] = (t < NP2 && in_padded(A.d, i, j)) ? pidx(A.d, i, j, 0) : -1;
+    base[r] = (t >= 0 && in_padded(A.d, i, j)) ? pidx(A.d, i, j, 0) : -1;
   }
 }
 
@@ -167,26 +194,20 @@ __device__ __forceinline__ void store_prims(const Args& A, Smem& sm, int slot, c
   const ConstsF& c = A.c;
 #pragma unroll
   for (int r = 0; r < NLOAD; ++r) {
-    const int t = threadIdx.x + r * NT;
-    if (t < NP2) {
+    const int t = load_point(r);
+    if (t >= 0) {
       const float rp = f64_to_f32(reg[r][0] - 1.0);
       const float m1 = f64_to_f32(reg[r][1]), m2 = f64_to_f32(reg[r][2]), m3 = f64_to_f32(reg[r][3]);
       const float ep = f64_to_f32(reg[r][4] - c.e_inf);
-      const float rho = rp + 1.f;
-      const float ir = f_rcp(rho);
-      const float u = m1 * ir, v = m2 * ir, w = m3 * ir;
-      const float pp = c.gm1 * (ep - 0.5f * (m1 * u + m2 * v + m3 * w));
-      const float T = c.gamma * (pp + c.p_inf) * ir;
+      const float ir = f_rcp(rp + 1.f);
+      const float pp = c.gm1 * (ep - 0.5f * ir * (m1 * m1 + m2 * m2 + m3 * m3));
       float* P = &sm.prim[slot][0][0];
       P[F_R * NP2 + t] = rp;
       P[1 * NP2 + t] = m1;
       P[2 * NP2 + t] = m2;
       P[3 * NP2 + t] = m3;
       P[F_E * NP2 + t] = ep;
-      P[F_U * NP2 + t] = u;
-      P[F_V * NP2 + t] = v;
-      P[F_W * NP2 + t] = w;
-      P[F_T * NP2 + t] = T;
+      P[F_I * NP2 + t] = ir;
       P[F_P * NP2 + t] = pp;
     }
   }
@@ -205,16 +226,22 @@ __device__ __forceinline__ void load_metrics(const Args& A, long long nb, int q,
 }
 
 // Nodal fluxes, spectral radii and sensors of one node of plane q (slots
-// s_m, s_0, s_p of planes q-1, q, q+1) at halo-1 index t.
+// s_m, s_0, s_p of planes q-1, q, q+1) at halo-1 index t, into ring slot g.
 __device__ void nodal(const Args& A, Smem& sm, long long nb, const float met[10], int s_m, int s_0, int s_p, int g) {
   const ConstsF& c = A.c;
   const int t = threadIdx.x;
   const int x1 = t % H1X, y1 = t / H1X;
+  const bool tile = x1 >= 1 && x1 <= TX && y1 >= 1 && y1 <= TY;
+  const int o = (y1 - 1) * TX + (x1 - 1);
   const int c2 = (y1 + 1) * H2X + (x1 + 1);
-  float* Fo = &sm.flux[g][0][0];
+  float* Fx = &sm.fxy[g][0][0];
+  float* Fz = &sm.fz[g][0][0];
   if (nb < 0) {
 #pragma unroll 1
-    for (int f = 0; f < NGF; ++f) Fo[f * NP1 + t] = 0.f;
+    for (int f = 0; f < NXF; ++f) Fx[f * NP1 + t] = 0.f;
+    if (tile)
+#pragma unroll 1
+      for (int f = 0; f < NZF; ++f) Fz[f * NOUT + o] = 0.f;
     return;
   }
   float S[3][3];
@@ -227,85 +254,128 @@ __device__ void nodal(const Args& A, Smem& sm, long long nb, const float met[10]
   const float* P0 = &sm.prim[s_0][0][0];
   const float* Pm = &sm.prim[s_m][0][0];
   const float* Pp = &sm.prim[s_p][0][0];
-  // gradients of u, v, w, T: L[n][jj] = (1/V) sum_dir S^dir_jj delta_dir f_n
+  // u, v, w, T at a node of the ring (plane P, halo-2 index cc)
+  auto uvwT = [&](const float* P, int cc, float f[4]) {
+    const float ir = P[F_I * NP2 + cc];
+    f[0] = P[1 * NP2 + cc] * ir;
+    f[1] = P[2 * NP2 + cc] * ir;
+    f[2] = P[3 * NP2 + cc] * ir;
+    f[3] = c.gamma * (P[F_P * NP2 + cc] + c.p_inf) * ir;
+  };
+  // gradients of u, v, w, T: L[n][j] = sum_dir (S^dir_j / (2V)) (f_{+} - f_{-})
+  const float h = 0.5f * iV;
+  float fxp[4], fxm[4], fyp[4], fym[4], fzp[4], fzm[4];
+  uvwT(P0, c2 + 1, fxp);
+  uvwT(P0, c2 - 1, fxm);
+  uvwT(P0, c2 + H2X, fyp);
+  uvwT(P0, c2 - H2X, fym);
+  uvwT(Pp, c2, fzp);
+  uvwT(Pm, c2, fzm);
   float L[4][3];
 #pragma unroll
   for (int n = 0; n < 4; ++n) {
-    const int f = F_U + n;
-    const float dx = 0.5f * (P0[f * NP2 + c2 + 1] - P0[f * NP2 + c2 - 1]);
-    const float dy = 0.5f * (P0[f * NP2 + c2 + H2X] - P0[f * NP2 + c2 - H2X]);
-    const float dz = 0.5f * (Pp[f * NP2 + c2] - Pm[f * NP2 + c2]);
+    const float dx = fxp[n] - fxm[n], dy = fyp[n] - fym[n], dz = fzp[n] - fzm[n];
 #pragma unroll
-    for (int jj = 0; jj < 3; ++jj) L[n][jj] = iV * (S[0][jj] * dx + S[1][jj] * dy + S[2][jj] * dz);
+    for (int jj = 0; jj < 3; ++jj) L[n][jj] = h * (S[0][jj] * dx + S[1][jj] * dy + S[2][jj] * dz);
   }
   const float rho = P0[F_R * NP2 + c2] + 1.f;
   const float m1 = P0[1 * NP2 + c2], m2 = P0[2 * NP2 + c2], m3 = P0[3 * NP2 + c2];
-  const float u = P0[F_U * NP2 + c2], v = P0[F_V * NP2 + c2], w = P0[F_W * NP2 + c2];
-  const float T = P0[F_T * NP2 + c2], pp = P0[F_P * NP2 + c2];
+  float f0[4];
+  uvwT(P0, c2, f0);
+  const float u = f0[0], v = f0[1], w = f0[2], T = f0[3];
+  const float pp = P0[F_P * NP2 + c2];
   const float ep = P0[F_E * NP2 + c2];
   const float a = f_sqrt(T);
   const float mu = c.mu_ref * (T * a) * c.sut_num * f_rcp(T + c.S_hat);
-  float Sij[3][3];
-#pragma unroll
-  for (int x = 0; x < 3; ++x)
-#pragma unroll
-    for (int y = 0; y < 3; ++y) Sij[x][y] = 0.5f * (L[x][y] + L[y][x]);
-  const float div = Sij[0][0] + Sij[1][1] + Sij[2][2];
-  float SS = 0.f;
-#pragma unroll
-  for (int x = 0; x < 3; ++x)
-#pragma unroll
-    for (int y = 0; y < 3; ++y) SS += Sij[x][y] * Sij[x][y];
+  // strain rate (symmetric), eddy viscosity, stresses
+  const float s11 = L[0][0], s22 = L[1][1], s33 = L[2][2];
+  const float s12 = 0.5f * (L[0][1] + L[1][0]), s13 = 0.5f * (L[0][2] + L[2][0]), s23 = 0.5f * (L[1][2] + L[2][1]);
+  const float div = s11 + s22 + s33;
+  const float SS = s11 * s11 + s22 * s22 + s33 * s33 + 2.f * (s12 * s12 + s13 * s13 + s23 * s23);
   const float Smod = f_sqrt(2.f * SS);
   const float csd = c.C_s * cbrt_pos(V);
   const float mu_sgs = rho * (csd * csd) * Smod;
-  const float mu_eff = mu + mu_sgs;
+  const float m2e = 2.f * (mu + mu_sgs);
   const float k_eff = mu * c.k_lam + mu_sgs * c.k_sgs;
   const float d3 = div * (1.f / 3.f);
-  float tau[3][3];
-#pragma unroll
-  for (int x = 0; x < 3; ++x)
-#pragma unroll
-    for (int y = 0; y < 3; ++y) tau[x][y] = 2.f * mu_eff * (Sij[x][y] - (x == y ? d3 : 0.f));
-  float F[3][4];
-#pragma unroll
-  for (int jj = 0; jj < 3; ++jj) {
-    F[jj][0] = tau[0][jj];
-    F[jj][1] = tau[1][jj];
-    F[jj][2] = tau[2][jj];
-    F[jj][3] = u * tau[0][jj] + v * tau[1][jj] + w * tau[2][jj] + k_eff * L[3][jj];
-  }
+  const float t11 = m2e * (s11 - d3), t22 = m2e * (s22 - d3), t33 = m2e * (s33 - d3);
+  const float t12 = m2e * s12, t13 = m2e * s13, t23 = m2e * s23;
+  // Cartesian viscous fluxes F_x, F_y, F_z (momentum x, y, z; energy)
+  const float F[3][4] = {{t11, t12, t13, u * t11 + v * t12 + w * t13 + k_eff * L[3][0]},
+                         {t12, t22, t23, u * t12 + v * t22 + w * t23 + k_eff * L[3][1]},
+                         {t13, t23, t33, u * t13 + v * t23 + w * t33 + k_eff * L[3][2]}};
   const float h0 = ep + pp + c.ep_inf;   // e + p
-  float lam[3];
+  float lam[3], H[3][5];
 #pragma unroll
   for (int dir = 0; dir < 3; ++dir) {
     const float U = S[dir][0] * u + S[dir][1] * v + S[dir][2] * w;
     const float smag = f_sqrt(S[dir][0] * S[dir][0] + S[dir][1] * S[dir][1] + S[dir][2] * S[dir][2]);
     lam[dir] = fabsf(U) + a * smag;
-    const int gh = G_HX + 5 * dir;
-    Fo[(gh + 0) * NP1 + t] = rho * U;
-    const float fv0 = S[dir][0] * F[0][0] + S[dir][1] * F[1][0] + S[dir][2] * F[2][0];
-    const float fv1 = S[dir][0] * F[0][1] + S[dir][1] * F[1][1] + S[dir][2] * F[2][1];
-    const float fv2 = S[dir][0] * F[0][2] + S[dir][1] * F[1][2] + S[dir][2] * F[2][2];
-    const float fv3 = S[dir][0] * F[0][3] + S[dir][1] * F[1][3] + S[dir][2] * F[2][3];
-    Fo[(gh + 1) * NP1 + t] = m1 * U + pp * S[dir][0] - fv0;
-    Fo[(gh + 2) * NP1 + t] = m2 * U + pp * S[dir][1] - fv1;
-    Fo[(gh + 3) * NP1 + t] = m3 * U + pp * S[dir][2] - fv2;
-    Fo[(gh + 4) * NP1 + t] = h0 * U - fv3;
+    H[dir][0] = rho * U;
+    H[dir][1] = m1 * U + pp * S[dir][0] - (S[dir][0] * F[0][0] + S[dir][1] * F[1][0] + S[dir][2] * F[2][0]);
+    H[dir][2] = m2 * U + pp * S[dir][1] - (S[dir][0] * F[0][1] + S[dir][1] * F[1][1] + S[dir][2] * F[2][1]);
+    H[dir][3] = m3 * U + pp * S[dir][2] - (S[dir][0] * F[0][2] + S[dir][1] * F[1][2] + S[dir][2] * F[2][2]);
+    H[dir][4] = h0 * U - (S[dir][0] * F[0][3] + S[dir][1] * F[1][3] + S[dir][2] * F[2][3]);
   }
-  const float t0 = cbrt_pos(lam[0]), t1 = cbrt_pos(lam[1]), t2 = cbrt_pos(lam[2]);
-  Fo[(G_L + 0) * NP1 + t] = lam[0] + t0 * (t1 * t1 + t2 * t2);
-  Fo[(G_L + 1) * NP1 + t] = lam[1] + t1 * (t0 * t0 + t2 * t2);
-  Fo[(G_L + 2) * NP1 + t] = lam[2] + t2 * (t0 * t0 + t1 * t1);
+  const float r0 = cbrt_pos(lam[0]), r1 = cbrt_pos(lam[1]), r2 = cbrt_pos(lam[2]);
   // pressure sensors (p' = p - p_inf; denominators add 4 p_inf back)
   const float* pr0 = P0 + F_P * NP2;
   const float pxm = pr0[c2 - 1], pxp = pr0[c2 + 1], pym = pr0[c2 - H2X], pyp = pr0[c2 + H2X];
   const float pzm = Pm[F_P * NP2 + c2], pzp = Pp[F_P * NP2 + c2];
   const float p4 = 4.f * c.p_inf;
-  Fo[(G_N + 0) * NP1 + t] = fabsf(pxp - 2.f * pp + pxm) * f_rcp(pxp + 2.f * pp + pxm + p4);
-  Fo[(G_N + 1) * NP1 + t] = fabsf(pyp - 2.f * pp + pym) * f_rcp(pyp + 2.f * pp + pym + p4);
-  Fo[(G_N + 2) * NP1 + t] = fabsf(pzp - 2.f * pp + pzm) * f_rcp(pzp + 2.f * pp + pzm + p4);
-  Fo[G_IV * NP1 + t] = iV;
+#pragma unroll
+  for (int m = 0; m < 5; ++m) {
+    Fx[(X_HX + m) * NP1 + t] = H[0][m];
+    Fx[(X_HY + m) * NP1 + t] = H[1][m];
+  }
+  Fx[X_LX * NP1 + t] = lam[0] + r0 * (r1 * r1 + r2 * r2);
+  Fx[X_LY * NP1 + t] = lam[1] + r1 * (r0 * r0 + r2 * r2);
+  Fx[X_NX * NP1 + t] = fabsf(pxp - 2.f * pp + pxm) * f_rcp(pxp + 2.f * pp + pxm + p4);
+  Fx[X_NY * NP1 + t] = fabsf(pyp - 2.f * pp + pym) * f_rcp(pyp + 2.f * pp + pym + p4);
+  if (tile) {
+#pragma unroll
+    for (int m = 0; m < 5; ++m) Fz[(Z_HZ + m) * NOUT + o] = H[2][m];
+    Fz[Z_L * NOUT + o] = lam[2] + r2 * (r0 * r0 + r1 * r1);
+    Fz[Z_N * NOUT + o] = fabsf(pzp - 2.f * pp + pzm) * f_rcp(pzp + 2.f * pp + pzm + p4);
+    Fz[Z_IV * NOUT + o] = iV;
+  }
+}
+
+// The xi and eta dissipation faces of one plane (ring slots: prim s_0, fluxes g),
+// each computed once by one thread.
+__device__ void plane_faces(const Args& A, Smem& sm, int s_0, int g) {
+  const float* P = &sm.prim[s_0][0][0];
+  const float* Fx = &sm.fxy[g][0][0];
+  for (int e = threadIdx.x; e < NFACE; e += NT) {
+    float qm[5], q0[5], q1[5], q2[5], out[5];
+    if (e < NFX) {
+      const int oy = e / (TX + 1), fx = e % (TX + 1);
+      const int a = (oy + 1) * H1X + fx;           // halo-1 index of the left node
+      const int cq = (oy + 2) * H2X + fx + 1;      // halo-2 index of the left node
+#pragma unroll
+      for (int m = 0; m < 5; ++m) {
+        qm[m] = P[m * NP2 + cq - 1]; q0[m] = P[m * NP2 + cq]; q1[m] = P[m * NP2 + cq + 1]; q2[m] = P[m * NP2 + cq + 2];
+      }
+      face_flux(A.c, Fx[X_LX * NP1 + a], Fx[X_LX * NP1 + a + 1], Fx[X_NX * NP1 + a], Fx[X_NX * NP1 + a + 1],
+                qm, q0, q1, q2, out);
+#pragma unroll
+      for (int m = 0; m < 5; ++m) sm.dx[m][e] = out[m];
+    } else {
+      const int e2 = e - NFX;
+      const int fy = e2 / TX, ox = e2 % TX;
+      const int a = fy * H1X + ox + 1;             // halo-1 index of the lower node
+      const int cq = (fy + 1) * H2X + ox + 2;      // halo-2 index of the lower node
+#pragma unroll
+      for (int m = 0; m < 5; ++m) {
+        qm[m] = P[m * NP2 + cq - H2X]; q0[m] = P[m * NP2 + cq]; q1[m] = P[m * NP2 + cq + H2X];
+        q2[m] = P[m * NP2 + cq + 2 * H2X];
+      }
+      face_flux(A.c, Fx[X_LY * NP1 + a], Fx[X_LY * NP1 + a + H1X], Fx[X_NY * NP1 + a], Fx[X_NY * NP1 + a + H1X],
+                qm, q0, q1, q2, out);
+#pragma unroll
+      for (int m = 0; m < 5; ++m) sm.dy[m][e2] = out[m];
+    }
+  }
 }
 
 __device__ __forceinline__ void load_q(const float* P, int c2, float q[5]) {
@@ -331,6 +401,7 @@ __global__ void __launch_bounds__(NT, kMinBlocks) k_fused32(Args A) {
   const bool adv = outv && (d.topo != JZ_TOPO_JET || (oi >= 1 && oi <= d.ni - 2 && oj >= 1 && oj <= d.nj - 2));
   const int c1 = (oy + 1) * H1X + (ox + 1);
   const int c2 = (oy + 2) * H2X + (ox + 2);
+  static_assert(NT >= NOUT, "output threads");
 
   long long lb[NLOAD];
   load_bases(A, i0, j0, lb);
@@ -343,9 +414,9 @@ __global__ void __launch_bounds__(NT, kMinBlocks) k_fused32(Args A) {
   double reg[NLOAD][5];
   // prime: planes k0-2, k0-1 into the ring, plane k0 into registers
   prefetch(A, lb, k0 - 2, reg);
-  store_prims(A, sm, ring3(k0 - 2), reg);
+  store_prims(A, sm, ring(k0 - 2), reg);
   prefetch(A, lb, k0 - 1, reg);
-  store_prims(A, sm, ring3(k0 - 1), reg);
+  store_prims(A, sm, ring(k0 - 1), reg);
   prefetch(A, lb, k0, reg);
 
   float Hz_prev[5] = {0, 0, 0, 0, 0};   // H^zeta(p-1)
@@ -359,46 +430,50 @@ __global__ void __launch_bounds__(NT, kMinBlocks) k_fused32(Args A) {
     // (a) metrics of plane p+1 (used in (b)); plane p+2 -> ring; prefetch plane p+3
     float met[10];
     load_metrics(A, nb, p + 1, met);
-    store_prims(A, sm, ring3(p + 2), reg);
+    // L2 hints one plane ahead: metrics of plane p+2 (next iteration's nodal work)
+    // and Q^n of plane p+1 (next iteration's update)
+    if (nb >= 0 && p + 2 <= k1) {
+      const long long pm = nb + (long long)(p + 2) * d.sk;
+#pragma unroll
+      for (int f = 0; f < 10; ++f) prefetch_l2(A.S[f] + pm);
+    }
+    if (adv && !A.rhs && p + 1 < k1) {
+      const long long pq = ob + (long long)(p + 1) * d.sk;
+#pragma unroll
+      for (int m = 0; m < 5; ++m) prefetch_l2(A.qn[m] + pq);
+    }
+    store_prims(A, sm, ring(p + 2), reg);
     if (p + 3 <= k1 + 1) prefetch(A, lb, p + 3, reg);
     __syncthreads();
-    // (b) nodal quantities of plane p+1
-    nodal(A, sm, nb, met, ring3(p), ring3(p + 1), ring3(p + 2), (p + 1) & 1);
+    // (b) nodal quantities of plane p+1, then the xi/eta faces of plane p
+    nodal(A, sm, nb, met, ring(p), ring(p + 1), ring(p + 2), (p + 1) & 1);
+    plane_faces(A, sm, ring(p), p & 1);
     __syncthreads();
     // (c) zeta face p+1/2 and the output plane p
     if (outth) {
-      const float* Fp1 = &sm.flux[(p + 1) & 1][0][0];
-      const float* P0 = &sm.prim[ring3(p)][0][0];
-      const float* P1 = &sm.prim[ring3(p + 1)][0][0];
-      const float* P2 = &sm.prim[ring3(p + 2)][0][0];
-      const float Lz1 = Fp1[(G_L + 2) * NP1 + c1], Nz1 = Fp1[(G_N + 2) * NP1 + c1];
+      const float* Z0 = &sm.fz[p & 1][0][0];
+      const float* Z1 = &sm.fz[(p + 1) & 1][0][0];
+      const float* P0 = &sm.prim[ring(p)][0][0];
+      const float* P1 = &sm.prim[ring(p + 1)][0][0];
+      const float* P2 = &sm.prim[ring(p + 2)][0][0];
+      const float Lz1 = Z1[Z_L * NOUT + t], Nz1 = Z1[Z_N * NOUT + t];
       float q0[5], q1[5], q2[5], Dz[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
       load_q(P0, c2, q0);
       load_q(P1, c2, q1);
       load_q(P2, c2, q2);
       if (p >= k0 - 1) face_flux(c, Lz, Lz1, Nz, Nz1, Qz_prev, q0, q1, q2, Dz);
       if (p >= k0 && outv) {
-        const float* F0 = &sm.flux[p & 1][0][0];
+        const float* F0 = &sm.fxy[p & 1][0][0];
+        const int ex = oy * (TX + 1) + ox, ey = oy * TX + ox;
+        const float iV = Z0[Z_IV * NOUT + t];
         float R[5];
-        // xi faces i -/+ 1/2 and eta faces j -/+ 1/2
-        float a0[5], a1[5], a2[5], a3[5], Dxm[5], Dxp[5], Dym[5], Dyp[5];
-        load_q(P0, c2 - 2, a0); load_q(P0, c2 - 1, a1); load_q(P0, c2 + 1, a2); load_q(P0, c2 + 2, a3);
-        face_flux(c, F0[G_L * NP1 + c1 - 1], F0[G_L * NP1 + c1], F0[G_N * NP1 + c1 - 1], F0[G_N * NP1 + c1],
-                  a0, a1, q0, a2, Dxm);
-        face_flux(c, F0[G_L * NP1 + c1], F0[G_L * NP1 + c1 + 1], F0[G_N * NP1 + c1], F0[G_N * NP1 + c1 + 1],
-                  a1, q0, a2, a3, Dxp);
-        load_q(P0, c2 - 2 * H2X, a0); load_q(P0, c2 - H2X, a1); load_q(P0, c2 + H2X, a2);
-        load_q(P0, c2 + 2 * H2X, a3);
-        face_flux(c, F0[(G_L + 1) * NP1 + c1 - H1X], F0[(G_L + 1) * NP1 + c1], F0[(G_N + 1) * NP1 + c1 - H1X],
-                  F0[(G_N + 1) * NP1 + c1], a0, a1, q0, a2, Dym);
-        face_flux(c, F0[(G_L + 1) * NP1 + c1], F0[(G_L + 1) * NP1 + c1 + H1X], F0[(G_N + 1) * NP1 + c1],
-                  F0[(G_N + 1) * NP1 + c1 + H1X], a1, q0, a2, a3, Dyp);
-        const float iV = F0[G_IV * NP1 + c1];
 #pragma unroll
         for (int m = 0; m < 5; ++m) {
-          float acc = 0.5f * (F0[(G_HX + m) * NP1 + c1 + 1] - F0[(G_HX + m) * NP1 + c1 - 1]) - (Dxp[m] - Dxm[m]);
-          acc += 0.5f * (F0[(G_HY + m) * NP1 + c1 + H1X] - F0[(G_HY + m) * NP1 + c1 - H1X]) - (Dyp[m] - Dym[m]);
-          acc += 0.5f * (Fp1[(G_HZ + m) * NP1 + c1] - Hz_prev[m]) - (Dz[m] - Dz_prev[m]);
+          float acc = 0.5f * (F0[(X_HX + m) * NP1 + c1 + 1] - F0[(X_HX + m) * NP1 + c1 - 1]) -
+                      (sm.dx[m][ex + 1] - sm.dx[m][ex]);
+          acc += 0.5f * (F0[(X_HY + m) * NP1 + c1 + H1X] - F0[(X_HY + m) * NP1 + c1 - H1X]) -
+                 (sm.dy[m][ey + TX] - sm.dy[m][ey]);
+          acc += 0.5f * (Z1[(Z_HZ + m) * NOUT + t] - Hz_prev[m]) - (Dz[m] - Dz_prev[m]);
           R[m] = acc * iV;
         }
         const long long pp = ob + (long long)p * d.sk;
@@ -439,14 +514,15 @@ __global__ void __launch_bounds__(NT, kMinBlocks) k_fused32(Args A) {
       // rotate the zeta registers
 #pragma unroll
       for (int m = 0; m < 5; ++m) {
-        Hz_prev[m] = sm.flux[p & 1][G_HZ + m][c1];
+        Hz_prev[m] = Z0[(Z_HZ + m) * NOUT + t];
         Dz_prev[m] = Dz[m];
         Qz_prev[m] = q0[m];
       }
       Lz = Lz1;
       Nz = Nz1;
     }
-    __syncthreads();
+    // no barrier here: the next plane's conversion writes ring slot p+3, which no
+    // thread reads in this iteration; the barrier after it orders the flux rings.
   }
   if (A.want_res || A.want_rate) {
     __shared__ float red[2][NT / 32];
