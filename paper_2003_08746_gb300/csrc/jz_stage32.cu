@@ -40,6 +40,8 @@ constexpr int H1X = TX + 2, H1Y = TY + 2, NP1 = H1X * H1Y;   // 32 x 10
 constexpr int H2X = TX + 4, H2Y = TY + 4, NP2 = H2X * H2Y;   // 34 x 12
 constexpr int NT = NP1;                                      // threads per CTA
 constexpr int NOUT = TX * TY;
+constexpr int NOT = 32 * TY;                                 // output threads: one warp per row
+static_assert(TX <= 32 && NOT <= NT, "one warp per output row");
 constexpr int NLOAD = (NP2 + NT - 1) / NT;                   // halo-2 points per thread
 
 // primitive ring: rho' = rho - 1, m1, m2, m3, e' = e - e_inf, 1/rho, p' = p - p_inf
@@ -154,14 +156,21 @@ struct Args {
 };
 
 // Halo-2 point loaded by this thread in round r: round 0 covers points 0..NT-1;
-// round 1 goes first to the threads that have no output node (they are idle in
-// the output phase), then to the lowest threads.  -1: none.
+// round 1 goes first to the threads that have no output node (the warps past
+// the output rows, then the unused lanes of the output warps), then to the
+// lowest threads.  -1: none.
 __device__ __forceinline__ int load_point(int r) {
   const int t = threadIdx.x;
   if (r == 0) return t < NP2 ? t : -1;
-  const int extra = NT - NOUT;                       // threads without an output node
-  if (t >= NOUT) return NT + (t - NOUT) < NP2 ? NT + (t - NOUT) : -1;
-  return NT + extra + t < NP2 ? NT + extra + t : -1;
+  int q;
+  if (t >= NOT) {
+    q = NT + (t - NOT);
+  } else if ((t & 31) >= TX) {
+    q = NT + (NT - NOT) + (t >> 5) * (32 - TX) + ((t & 31) - TX);
+  } else {
+    q = NT + (NT - NOT) + TY * (32 - TX) + t;
+  }
+  return q < NP2 ? q : -1;
 }
 
 // Padded index at k = 0 of this thread's halo-2 load points (-1: outside the padded box).
@@ -342,14 +351,20 @@ __device__ void nodal(const Args& A, Smem& sm, long long nb, const float met[10]
 }
 
 // The xi and eta dissipation faces of one plane (ring slots: prim s_0, fluxes g),
-// each computed once by one thread.
+// each computed once by one thread.  Tasks are laid out one 32-lane row per
+// face row so that a warp touches one shared-memory row (no bank conflicts).
+constexpr int NTX = 32 * TY, NTY = 32 * (TY + 1);
+static_assert(TX + 1 <= 32, "xi face row fits a warp");
+
 __device__ void plane_faces(const Args& A, Smem& sm, int s_0, int g) {
   const float* P = &sm.prim[s_0][0][0];
   const float* Fx = &sm.fxy[g][0][0];
-  for (int e = threadIdx.x; e < NFACE; e += NT) {
+  for (int task = threadIdx.x; task < NTX + NTY; task += NT) {
     float qm[5], q0[5], q1[5], q2[5], out[5];
-    if (e < NFX) {
-      const int oy = e / (TX + 1), fx = e % (TX + 1);
+    if (task < NTX) {
+      const int oy = task >> 5, fx = task & 31;
+      if (fx > TX) continue;
+      const int e = oy * (TX + 1) + fx;
       const int a = (oy + 1) * H1X + fx;           // halo-1 index of the left node
       const int cq = (oy + 2) * H2X + fx + 1;      // halo-2 index of the left node
 #pragma unroll
@@ -361,8 +376,9 @@ __device__ void plane_faces(const Args& A, Smem& sm, int s_0, int g) {
 #pragma unroll
       for (int m = 0; m < 5; ++m) sm.dx[m][e] = out[m];
     } else {
-      const int e2 = e - NFX;
-      const int fy = e2 / TX, ox = e2 % TX;
+      const int fy = (task - NTX) >> 5, ox = (task - NTX) & 31;
+      if (ox >= TX) continue;
+      const int e2 = fy * TX + ox;
       const int a = fy * H1X + ox + 1;             // halo-1 index of the lower node
       const int cq = (fy + 1) * H2X + ox + 2;      // halo-2 index of the lower node
 #pragma unroll
@@ -394,14 +410,14 @@ __global__ void __launch_bounds__(NT, kMinBlocks) k_fused32(Args A) {
   const int k0 = blockIdx.z * A.kchunk;
   const int k1 = min(k0 + A.kchunk, d.nk);          // output planes [k0, k1)
   const int t = threadIdx.x;
-  const bool outth = t < NOUT;
-  const int ox = t % TX, oy = t / TX;
+  const int ox = t & 31, oy = t >> 5;
+  const bool outth = t < NOT && ox < TX;
+  const int o = oy * TX + ox;                       // tile index of the output node
   const int oi = i0 + ox, oj = j0 + oy;
   const bool outv = outth && oi < d.ni && oj < d.nj;
   const bool adv = outv && (d.topo != JZ_TOPO_JET || (oi >= 1 && oi <= d.ni - 2 && oj >= 1 && oj <= d.nj - 2));
   const int c1 = (oy + 1) * H1X + (ox + 1);
   const int c2 = (oy + 2) * H2X + (ox + 2);
-  static_assert(NT >= NOUT, "output threads");
 
   long long lb[NLOAD];
   load_bases(A, i0, j0, lb);
@@ -456,7 +472,7 @@ __global__ void __launch_bounds__(NT, kMinBlocks) k_fused32(Args A) {
       const float* P0 = &sm.prim[ring(p)][0][0];
       const float* P1 = &sm.prim[ring(p + 1)][0][0];
       const float* P2 = &sm.prim[ring(p + 2)][0][0];
-      const float Lz1 = Z1[Z_L * NOUT + t], Nz1 = Z1[Z_N * NOUT + t];
+      const float Lz1 = Z1[Z_L * NOUT + o], Nz1 = Z1[Z_N * NOUT + o];
       float q0[5], q1[5], q2[5], Dz[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
       load_q(P0, c2, q0);
       load_q(P1, c2, q1);
@@ -465,7 +481,7 @@ __global__ void __launch_bounds__(NT, kMinBlocks) k_fused32(Args A) {
       if (p >= k0 && outv) {
         const float* F0 = &sm.fxy[p & 1][0][0];
         const int ex = oy * (TX + 1) + ox, ey = oy * TX + ox;
-        const float iV = Z0[Z_IV * NOUT + t];
+        const float iV = Z0[Z_IV * NOUT + o];
         float R[5];
 #pragma unroll
         for (int m = 0; m < 5; ++m) {
@@ -473,7 +489,7 @@ __global__ void __launch_bounds__(NT, kMinBlocks) k_fused32(Args A) {
                       (sm.dx[m][ex + 1] - sm.dx[m][ex]);
           acc += 0.5f * (F0[(X_HY + m) * NP1 + c1 + H1X] - F0[(X_HY + m) * NP1 + c1 - H1X]) -
                  (sm.dy[m][ey + TX] - sm.dy[m][ey]);
-          acc += 0.5f * (Z1[(Z_HZ + m) * NOUT + t] - Hz_prev[m]) - (Dz[m] - Dz_prev[m]);
+          acc += 0.5f * (Z1[(Z_HZ + m) * NOUT + o] - Hz_prev[m]) - (Dz[m] - Dz_prev[m]);
           R[m] = acc * iV;
         }
         const long long pp = ob + (long long)p * d.sk;
@@ -514,7 +530,7 @@ __global__ void __launch_bounds__(NT, kMinBlocks) k_fused32(Args A) {
       // rotate the zeta registers
 #pragma unroll
       for (int m = 0; m < 5; ++m) {
-        Hz_prev[m] = Z0[(Z_HZ + m) * NOUT + t];
+        Hz_prev[m] = Z0[(Z_HZ + m) * NOUT + o];
         Dz_prev[m] = Dz[m];
         Qz_prev[m] = q0[m];
       }

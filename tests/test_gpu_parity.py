@@ -156,3 +156,57 @@ def test_jet_full_size_one_step(jz):
     e2, em = field_errors(got, ref.numpy())
     assert e2.max() <= TOL_L2, e2
     assert em.max() <= TOL_MAX, em
+
+
+def _window_residual(g, q, prm, i, j, k, W=5):
+    """Oracle residual at node (i, j, k) of a large grid from an (2W+1)^3 window around it.
+
+    The residual at a node depends on coordinates within 3 nodes and on the state within
+    2 nodes, so the window's own (wrapped, meaningless) ghost layers never reach its centre.
+    """
+    sl = (slice(k - W, k + W + 1), slice(j - W, j + W + 1), slice(i - W, i + W + 1))
+    xyz = np.ascontiguousarray(g.xyz[(slice(None),) + sl])
+    qw = np.ascontiguousarray(q[(slice(None),) + sl])
+    n = 2 * W + 1
+    grid = O.Grid(n, n, n, xyz, O.TOPO_PERIODIC, np.zeros((3, 3)))
+    R = O.residual_padded(grid, grid.pad(torch.from_numpy(qw)), O.Consts(prm))
+    return R[:, W, W, W].numpy()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32flux"])
+def test_full_size_sampled_residual(jz, precision):
+    """Jet 1000 x 400 x 500 (the benchmark workload, same launch configuration): the GPU
+    residual at 24 seeded interior nodes against the oracle on a window around each node."""
+    g, q, prm = W.make_workload("jet1000x400x500")
+    rng = np.random.Generator(np.random.PCG64(77))
+    q = q + 1e-3 * rng.standard_normal(q.shape) * np.array([1, 1, 1, 1, 1])[:, None, None, None]
+    grid = jz.Grid.from_workload(g)
+    prec = jz.JZ_PREC_FP64 if precision == "fp64" else jz.JZ_PREC_FP32FLUX
+    s = jz.Solver(grid, prm, prec)
+    qd = torch.from_numpy(q).cuda()
+    rd = torch.empty_like(qd)
+    s.residual(qd, rd)
+    nodes = [(int(rng.integers(6, g.ni - 6)), int(rng.integers(6, g.nj - 6)), int(rng.integers(6, g.nk - 6)))
+             for _ in range(24)]
+    tol = 1e-11 if precision == "fp64" else 2e-4
+    for (i, j, k) in nodes:
+        got = rd[:, k, j, i].cpu().numpy()
+        ref = _window_residual(g, q, prm, i, j, k)
+        scale = np.abs(ref).max()
+        assert np.abs(got - ref).max() <= tol * scale, (i, j, k, got, ref)
+    s.close()
+    grid.close()
+
+
+def test_jet_subsample_500_steps_fp64(jz):
+    """The 64 x 32 x 16 jet (the precision workload's subsample), 500 FP64 steps against the oracle."""
+    g, q, prm = W.make_workload("jet64x32x16")
+    grid = jz.Grid.from_workload(g)
+    s = jz.Solver(grid, prm)
+    s.set_state(q, 0.0)
+    s.step(500, stats=False)
+    got = s.get_state()
+    ref, _, _, _ = O.run(oracle_grid(g), torch.from_numpy(q), O.Consts(prm), 500)
+    e2, em = field_errors(got, ref.numpy())
+    print(f"jet64x32x16 FP64 500 steps vs oracle: rel L2 {e2}, rel max {em}")
+    assert e2.max() <= TOL_L2, e2
