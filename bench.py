@@ -39,11 +39,14 @@ FP64_PEAK_TFLOPS = 152 * 4 * 2.07e9 / 1e12
 # Algorithmic FP64 flops per point of each FP64 stage kernel (add/sub/mul = 1,
 # fused multiply-add = 2, divide/sqrt/cbrt = 1), counted from the operations
 # the method needs per node (each quantity once).
-FLOPS_PER_POINT = {"nodal": 82, "viscous": 272, "faces": 168, "update": 91}
+FLOPS_PER_POINT = {"nodal": 83, "viscous": 233, "faces": 168, "update": 76}
 # DRAM bytes per node of a kernel launch from an ncu capture (dram__bytes_read.sum +
 # dram__bytes_write.sum / nodes), scaled to the full launch by its node count;
-# profiles/k_viscous_fp64_jet256x128x64.md.
-TRAFFIC_PER_NODE = {"viscous": 347.0}
+# profiles/k_viscous_fp64_jet256x128x64.md (null until re-captured after a change).
+TRAFFIC_PER_NODE = {}
+# k_fused32: (123 + 4 x 170) / 5 DRAM bytes per node over a step's five launches
+# (stage 1 and stage 2 captures in profiles/k_fused32_jet256x128x64.md).
+TRAFFIC_FUSED32_PER_NODE = (123.0 + 4 * 170.0) / 5
 
 
 def _dist():
@@ -285,7 +288,7 @@ def main():
         variants["fp32flux"] = {
             "value": v32, "unit": "Gpoint-stage/s", "ms_per_step": r32["ms"] / args.steps, "dtype": "f32 flux / f64 state",
             "roofline": {"bound": "hbm", "kernel": "fused32", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s",
-                         "frac": gbs / hbm_peak, "traffic": None,
+                         "frac": gbs / hbm_peak, "traffic": TRAFFIC_FUSED32_PER_NODE * npts,
                          "algorithmic_bytes_per_point_stage": 152},
             "kernels": {k: {"ms_per_launch": v[0] / v[1], "launches": int(v[1]), "share": v[0] / tot32}
                         for k, v in r32["prof"].items() if v[1] > 0},

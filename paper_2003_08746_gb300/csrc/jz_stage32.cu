@@ -70,13 +70,14 @@ struct ConstsF {
 };
 
 // FP64 -> FP32 by bit manipulation (truncation toward zero; magnitudes below
-// 2^-126 flush to signed zero).  Valid for finite |x| < 2^128.
+// 2^-126 flush to signed zero).  Valid for finite |x| < 2^128.  Re-biasing the
+// exponent on the high word (e - 896 fits in 8 bits) lets one funnel shift pick
+// the FP32 exponent and the top 23 mantissa bits at once.
 __device__ __forceinline__ float f64_to_f32(double x) {
   const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
-  const int e8 = (int)((hi >> 20) & 0x7FFu) - 896;
-  const unsigned m = __funnelshift_l(lo, hi, 3) & 0x7FFFFFu;
-  const unsigned s = hi & 0x80000000u;
-  return __uint_as_float(e8 > 0 ? (s | ((unsigned)e8 << 23) | m) : s);
+  const unsigned f = __funnelshift_l(lo, hi - (896u << 20), 3);
+  const unsigned r = (f & 0x7FFFFFFFu) | (hi & 0x80000000u);
+  return __uint_as_float((hi << 1) >= (897u << 21) ? r : (hi & 0x80000000u));
 }
 
 // FP32 -> FP64, exact (subnormals flush to zero; Inf/NaN kept).
@@ -196,6 +197,16 @@ __device__ __forceinline__ void prefetch(const Args& A, const long long base[NLO
       reg[r][0] = 1.0; reg[r][1] = 0.0; reg[r][2] = 0.0; reg[r][3] = 0.0; reg[r][4] = A.c.e_inf;
     }
   }
+}
+
+// Request this thread's halo-2 points of plane k into L2 (no registers held).
+__device__ __forceinline__ void l2_plane(const Args& A, const long long base[NLOAD], int k) {
+  const long long koff = (long long)k * A.d.sk;
+#pragma unroll
+  for (int r = 0; r < NLOAD; ++r)
+    if (base[r] >= 0)
+#pragma unroll
+      for (int m = 0; m < 5; ++m) prefetch_l2(A.qin[m] + base[r] + koff);
 }
 
 // Convert prefetched FP64 state to FP32 primitives in a ring slot.
@@ -427,13 +438,16 @@ __global__ void __launch_bounds__(NT, kMinBlocks) k_fused32(Args A) {
     nb = in_padded(d, i, j) ? pidx(d, i, j, 0) : -1;
   }
   const long long ob = outv ? pidx(d, oi, oj, 0) : 0;   // output node
-  double reg[NLOAD][5];
-  // prime: planes k0-2, k0-1 into the ring, plane k0 into registers
-  prefetch(A, lb, k0 - 2, reg);
-  store_prims(A, sm, ring(k0 - 2), reg);
-  prefetch(A, lb, k0 - 1, reg);
-  store_prims(A, sm, ring(k0 - 1), reg);
-  prefetch(A, lb, k0, reg);
+  // prime: planes k0-2, k0-1 into the ring; planes k0 and k0+1 requested into L2
+  {
+    double reg[NLOAD][5];
+    prefetch(A, lb, k0 - 2, reg);
+    store_prims(A, sm, ring(k0 - 2), reg);
+    prefetch(A, lb, k0 - 1, reg);
+    store_prims(A, sm, ring(k0 - 1), reg);
+  }
+  l2_plane(A, lb, k0);
+  l2_plane(A, lb, k0 + 1);
 
   float Hz_prev[5] = {0, 0, 0, 0, 0};   // H^zeta(p-1)
   float Dz_prev[5] = {0, 0, 0, 0, 0};   // d^zeta(p-1/2)
@@ -458,8 +472,12 @@ __global__ void __launch_bounds__(NT, kMinBlocks) k_fused32(Args A) {
 #pragma unroll
       for (int m = 0; m < 5; ++m) prefetch_l2(A.qn[m] + pq);
     }
-    store_prims(A, sm, ring(p + 2), reg);
-    if (p + 3 <= k1 + 1) prefetch(A, lb, p + 3, reg);
+    {
+      double reg[NLOAD][5];
+      prefetch(A, lb, p + 2, reg);                   // L2 hit: requested one plane earlier
+      store_prims(A, sm, ring(p + 2), reg);
+    }
+    if (p + 3 <= k1 + 1) l2_plane(A, lb, p + 3);
     __syncthreads();
     // (b) nodal quantities of plane p+1, then the xi/eta faces of plane p
     nodal(A, sm, nb, met, ring(p), ring(p + 1), ring(p + 2), (p + 1) & 1);
@@ -473,6 +491,13 @@ __global__ void __launch_bounds__(NT, kMinBlocks) k_fused32(Args A) {
       const float* P1 = &sm.prim[ring(p + 1)][0][0];
       const float* P2 = &sm.prim[ring(p + 2)][0][0];
       const float Lz1 = Z1[Z_L * NOUT + o], Nz1 = Z1[Z_N * NOUT + o];
+      // Q^n of this output node, requested before the zeta-face work that hides its latency
+      double qn_r[5];
+      const long long pp = ob + (long long)p * d.sk;
+      if (p >= k0 && adv && !A.rhs) {
+#pragma unroll
+        for (int m = 0; m < 5; ++m) qn_r[m] = __ldg(A.qn[m] + pp);
+      }
       float q0[5], q1[5], q2[5], Dz[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
       load_q(P0, c2, q0);
       load_q(P1, c2, q1);
@@ -492,7 +517,6 @@ __global__ void __launch_bounds__(NT, kMinBlocks) k_fused32(Args A) {
           acc += 0.5f * (Z1[(Z_HZ + m) * NOUT + o] - Hz_prev[m]) - (Dz[m] - Dz_prev[m]);
           R[m] = acc * iV;
         }
-        const long long pp = ob + (long long)p * d.sk;
         if (A.rhs) {
           const long long N = (long long)d.ni * d.nj * d.nk;
           const long long ridx = ((long long)p * d.nj + oj) * d.ni + oi;
@@ -502,7 +526,7 @@ __global__ void __launch_bounds__(NT, kMinBlocks) k_fused32(Args A) {
           double qnew[5];
 #pragma unroll
           for (int m = 0; m < 5; ++m) {
-            qnew[m] = __ldg(A.qn[m] + pp) - f32_to_f64(adt * R[m]);
+            qnew[m] = qn_r[m] - f32_to_f64(adt * R[m]);
             A.qout[m][pp] = qnew[m];
           }
           if (A.want_rate) {

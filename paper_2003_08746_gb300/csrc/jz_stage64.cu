@@ -54,9 +54,10 @@ __global__ void __launch_bounds__(kTPB) k_nodal(Dims d, Consts c, GridDev g, Wor
   if (!box_coord(b, blockIdx.x * (long long)blockDim.x + threadIdx.x, i, j, k)) return;
   const long long p = pidx(d, i, j, k);
   const double rho = q.q[0][p], m1 = q.q[1][p], m2 = q.q[2][p], m3 = q.q[3][p], e = q.q[4][p];
-  const double u = m1 / rho, v = m2 / rho, ww = m3 / rho;
+  const double ir = 1.0 / rho;                  // one reciprocal instead of four divisions
+  const double u = m1 * ir, v = m2 * ir, ww = m3 * ir;
   const double pr = c.gm1 * (e - 0.5 * (m1 * u + m2 * v + m3 * ww));
-  const double T = c.gamma * pr / rho;
+  const double T = c.gamma * pr * ir;
   const double a = sqrt(T);
   // Sutherland, eq. (sutherland), with T_inf = 1
   const double mu = c.mu_ref * (T * a) * c.sut_num / (T + c.S_hat);
@@ -88,29 +89,32 @@ __global__ void __launch_bounds__(kTPB) k_viscous(Dims d, Consts c, GridDev g, W
   for (int dir = 0; dir < 3; ++dir)
     for (int cc = 0; cc < 3; ++cc) S[dir][cc] = g.S[3 * dir + cc][p];
   const double iV = g.invV[p];
-  // L[n][j] = d f_n / d x_j = (1/V) sum_dir S^dir_j delta_dir f_n
+  // L[n][j] = d f_n / d x_j = sum_dir (S^dir_j / (2V)) (f_n[+dir] - f_n[-dir])
+  const double h = 0.5 * iV;
+  double St[3][3];
+  for (int dir = 0; dir < 3; ++dir)
+    for (int cc = 0; cc < 3; ++cc) St[dir][cc] = h * S[dir][cc];
   double L[4][3];
   for (int n = 0; n < 4; ++n) {
     double dd[3];
-    for (int dir = 0; dir < 3; ++dir) dd[dir] = 0.5 * (f[n][p + s[dir]] - f[n][p - s[dir]]);
-    for (int jj = 0; jj < 3; ++jj) L[n][jj] = iV * (S[0][jj] * dd[0] + S[1][jj] * dd[1] + S[2][jj] * dd[2]);
+    for (int dir = 0; dir < 3; ++dir) dd[dir] = f[n][p + s[dir]] - f[n][p - s[dir]];
+    for (int jj = 0; jj < 3; ++jj) L[n][jj] = St[0][jj] * dd[0] + St[1][jj] * dd[1] + St[2][jj] * dd[2];
   }
-  double Sij[3][3];
-  for (int a = 0; a < 3; ++a)
-    for (int bb = 0; bb < 3; ++bb) Sij[a][bb] = 0.5 * (L[a][bb] + L[bb][a]);
-  const double div = Sij[0][0] + Sij[1][1] + Sij[2][2];
-  double SS = 0.0;
-  for (int a = 0; a < 3; ++a)
-    for (int bb = 0; bb < 3; ++bb) SS = SS + Sij[a][bb] * Sij[a][bb];
+  // symmetric strain rate, |S|, Smagorinsky eddy viscosity, stresses
+  const double s11 = L[0][0], s22 = L[1][1], s33 = L[2][2];
+  const double s12 = 0.5 * (L[0][1] + L[1][0]), s13 = 0.5 * (L[0][2] + L[2][0]), s23 = 0.5 * (L[1][2] + L[2][1]);
+  const double div = s11 + s22 + s33;
+  const double SS = s11 * s11 + s22 * s22 + s33 * s33 + 2.0 * (s12 * s12 + s13 * s13 + s23 * s23);
   const double Smod = sqrt(2.0 * SS);
   const double mu = w.mu[p];
   const double csd = c.C_s * g.Delta[p];
   const double mu_sgs = q.q[0][p] * (csd * csd) * Smod;
-  const double mu_eff = mu + mu_sgs;
+  const double m2e = 2.0 * (mu + mu_sgs);
   const double k_eff = mu * c.k_lam + mu_sgs * c.k_sgs;
-  double tau[3][3];
-  for (int a = 0; a < 3; ++a)
-    for (int bb = 0; bb < 3; ++bb) tau[a][bb] = 2.0 * mu_eff * (Sij[a][bb] - (a == bb ? div / 3.0 : 0.0));
+  const double d3 = div * (1.0 / 3.0);
+  const double t11 = m2e * (s11 - d3), t22 = m2e * (s22 - d3), t33 = m2e * (s33 - d3);
+  const double t12 = m2e * s12, t13 = m2e * s13, t23 = m2e * s23;
+  const double tau[3][3] = {{t11, t12, t13}, {t12, t22, t23}, {t13, t23, t33}};
   const double vel[3] = {w.u[p], w.v[p], w.w[p]};
   // Cartesian viscous flux in direction jj: [tau_1j, tau_2j, tau_3j, u_i tau_ij + k dT/dx_j]
   double F[3][4];
@@ -172,13 +176,14 @@ __global__ void __launch_bounds__(kTPB) k_update(Dims d, GridDev g, Work64 w, St
     const double iV = g.invV[p];
     double R[5];
     for (int m = 0; m < 5; ++m) {
-      double acc = 0.0;
+      double dH = 0.0, dD = 0.0;
       for (int dir = 0; dir < 3; ++dir) {
         const double* H = w.H[dir][m];
         const double* D = w.D[dir][m];
-        acc = acc + 0.5 * (H[p + s[dir]] - H[p - s[dir]]) - (D[p] - D[p - s[dir]]);
+        dH += H[p + s[dir]] - H[p - s[dir]];
+        dD += D[p] - D[p - s[dir]];
       }
-      R[m] = acc * iV;
+      R[m] = (0.5 * dH - dD) * iV;
     }
     if (MODE == 0) {
       const double adt = alpha * sc->dt;
