@@ -42,10 +42,10 @@ FP64_PEAK_TFLOPS = 152 * 4 * 2.07e9 / 1e12
 FLOPS_PER_POINT = {"nodal": 83, "viscous": 233, "faces": 168, "update": 76}
 # DRAM bytes per node of a kernel launch from an ncu capture (dram__bytes_read.sum +
 # dram__bytes_write.sum / nodes), scaled to the full launch by its node count;
-# profiles/k_viscous_fp64_jet256x128x64.md (null until re-captured after a change).
-TRAFFIC_PER_NODE = {}
+# profiles/k_viscous_fp64_jet256x128x64.md: (541.0 + 226.6) MB over 258 x 130 x 66 nodes.
+TRAFFIC_PER_NODE = {"viscous": 346.7}
 # k_fused32: (123 + 4 x 170) / 5 DRAM bytes per node over a step's five launches
-# (stage 1 and stage 2 captures in profiles/k_fused32_jet256x128x64.md).
+# (stage 1 and stage 2 captures of the current kernel in profiles/k_fused32_jet256x128x64.md).
 TRAFFIC_FUSED32_PER_NODE = (123.0 + 4 * 170.0) / 5
 
 
@@ -162,6 +162,60 @@ def run_reference(args):
     return 0
 
 
+def run_paper_meshes(args, jz, W, torch):
+    """Single-GPU throughput on the paper's Table "mesh" shapes (nk = 360 unique azimuthal points)."""
+    free, total = torch.cuda.mem_get_info()
+    rows = []
+    for name in args.paper_meshes.split(","):
+        ni, nj = W.PAPER_MESHES[name]
+        nk = 360
+        npts = ni * nj * nk
+        row = {"mesh": name, "shape": [ni, nj, nk], "points": npts}
+        xyz = W.jet_grid_device(ni, nj, nk)
+        q = W.jet_state_device(xyz)
+        prm = W.jet_params(seed=2)
+        padded = ((ni + 4 + 3) // 4 * 4) * (nj + 4) * (nk + 4)
+        free, _ = torch.cuda.mem_get_info()
+        if 216 * padded > 0.9 * free:          # 18 grid fields + 9 metric scratch fields
+            row["fp32flux"] = row["fp64"] = None
+            rows.append(row)
+            print(json.dumps(row), flush=True)
+            continue
+        grid = jz.Grid(ni, nj, nk, xyz, W.TOPO_JET)
+        grid._xyz = None
+        del xyz
+        torch.cuda.empty_cache()
+        # solver bytes per padded node: FP32-flux 3 x 5 FP64 state fields + 10 FP32 metrics;
+        # FP64 3 x 5 state fields + 42 stage-scratch fields
+        for form, prec, per_node in (("fp32flux", jz.JZ_PREC_FP32FLUX, 160), ("fp64", jz.JZ_PREC_FP64, 456)):
+            free, _ = torch.cuda.mem_get_info()
+            if per_node * padded > 0.9 * free:
+                row[form] = None
+                continue
+            stream = torch.cuda.Stream()
+            s = jz.Solver(grid, prm, prec, stream=stream.cuda_stream)
+            s.set_state(q, 0.0)
+            for _ in range(max(args.warmup, 1)):
+                s.step(1, stats=False)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            s.step(args.steps, stats=False)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / args.steps
+            st = s.step(0, stats=True)
+            row[form] = {"ms_per_step": ms, "gpoint_stage_per_s": npts * 5 / (ms / 1e3) / 1e9, "min_p": st.min_p}
+            s.close()
+            torch.cuda.empty_cache()
+        grid.close()
+        del q
+        torch.cuda.empty_cache()
+        rows.append(row)
+        print(json.dumps(row), flush=True)
+    print(json.dumps({"paper_meshes": rows}), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -174,6 +228,8 @@ def main():
     ap.add_argument("--no-fp32", action="store_true", help="skip the FP32-flux variant")
     ap.add_argument("--fp32-only", action="store_true", help="time only the FP32-flux form (profiling runs)")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint variant")
+    ap.add_argument("--paper-meshes", default="", help="comma list of the paper's meshes (A..I) to time "
+                    "on one GPU instead of the default run, e.g. A,B,C,D,E,F,G")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -231,6 +287,9 @@ def main():
         final = torch.empty_like(q_dev)
         solver.get_state(final)
         return solver, dict(ms=t_max, prof=prof, clocks=clocks, stats=stats, final=final)
+
+    if args.paper_meshes:
+        return run_paper_meshes(args, jz, W, torch)
 
     if args.fp32_only:
         solver32, r32 = timed_form(jz.JZ_PREC_FP32FLUX, True)

@@ -400,6 +400,10 @@ __global__ void k_adj_inout(Dims d, Consts c, Inflow in, State q, Adj64 a, doubl
   const long long plane = (long long)d.nk * d.nj;
   double g0 = 0.0;                 // d J / d u_target (times U_j) at this entrance node
   long long tab = 0;
+  // temporal factors sin(omega_f t + psi_mf), uniform over the entrance: once per block
+  __shared__ double sn[kNF];
+  if (threadIdx.x < kNF) sn[threadIdx.x] = sin(in.omega[threadIdx.x % JZ_N_FREQ] * ts + in.psi[threadIdx.x]);
+  __syncthreads();
   if (t < 2 * nface) {
     const bool exit_plane = t >= nface;
     const long long tt = exit_plane ? t - nface : t;
@@ -409,7 +413,7 @@ __global__ void k_adj_inout(Dims d, Consts c, Inflow in, State q, Adj64 a, doubl
       tab = (long long)k * d.nj + j;
       double f = 0.0;
       for (int mf = 0; mf < kNF; ++mf)
-        f = f + in.amp[mf] * in.Gf[mf * plane + tab] * sin(in.omega[mf % JZ_N_FREQ] * ts + in.psi[mf]);
+        f = f + in.amp[mf] * in.Gf[mf * plane + tab] * sn[mf];
       const double ut = in.u0[tab] + c.jet_mach * f;
       double Q1[5];
       load5(q, p1, Q1);
@@ -472,7 +476,7 @@ __global__ void k_adj_inout(Dims d, Consts c, Inflow in, State q, Adj64 a, doubl
   // one atomic per parameter per block
   __shared__ double red[kNF][kTPB / 32];
   for (int f = 0; f < kNF; ++f) {
-    double x = g0 != 0.0 ? g0 * in.Gf[f * plane + tab] * sin(in.omega[f % JZ_N_FREQ] * ts + in.psi[f]) : 0.0;
+    double x = g0 != 0.0 ? g0 * in.Gf[f * plane + tab] * sn[f] : 0.0;
     for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
     if ((threadIdx.x & 31) == 0) red[f][threadIdx.x >> 5] = x;
   }

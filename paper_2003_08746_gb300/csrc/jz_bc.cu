@@ -54,18 +54,22 @@ __global__ void k_inout(Dims d, Consts c, Inflow in, State q, const Scalars* sc,
   const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   const int nj1 = d.nj - 1;
   const long long nface = (long long)nj1 * d.nk;
+  // the 32 temporal factors sin(omega_f t + psi_mf) at t_n + alpha dt are the same at every
+  // entrance node: one evaluation each per block
+  __shared__ double sn[kNF];
+  if (threadIdx.x < kNF) sn[threadIdx.x] = sin(in.omega[threadIdx.x % JZ_N_FREQ] * (sc->t + alpha * sc->dt) +
+                                               in.psi[threadIdx.x]);
+  __syncthreads();
   if (t >= 2 * nface) return;
   const bool exit_plane = t >= nface;
   const long long tt = exit_plane ? t - nface : t;
   const int j = 1 + (int)(tt % nj1), k = (int)(tt / nj1);
   if (!exit_plane) {
     // target: tanh profile + forcing at t_n + alpha dt
-    const double ts = sc->t + alpha * sc->dt;
     const long long tab = (long long)k * d.nj + j;
     const long long plane = (long long)d.nk * d.nj;
     double f = 0.0;
-    for (int mf = 0; mf < kNF; ++mf)
-      f = f + in.amp[mf] * in.Gf[mf * plane + tab] * sin(in.omega[mf % JZ_N_FREQ] * ts + in.psi[mf]);
+    for (int mf = 0; mf < kNF; ++mf) f = f + in.amp[mf] * in.Gf[mf * plane + tab] * sn[mf];
     const double ut = in.u0[tab] + c.jet_mach * f;
     const long long p1 = pidx(d, 1, j, k), pb = pidx(d, 0, j, k);
     const double rho1 = q.q[0][p1];

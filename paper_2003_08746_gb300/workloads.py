@@ -181,6 +181,46 @@ def jet_grid(ni: int, nj: int, nk: int, length: float = 30.0, radius: float = 10
     return Grid(ni, nj, nk, np.ascontiguousarray(xyz), TOPO_JET, np.zeros((3, 3)))
 
 
+def jet_grid_device(ni: int, nj: int, nk: int, device="cuda", length: float = 30.0, radius: float = 10.0,
+                    radial_ratio: float = 10.0, axial_stretch: bool = False):
+    """The jet_grid recipe built on a torch device (for meshes too large to build quickly
+    on the host): the 1-D axes come from the same NumPy code, the 3-D coordinate array
+    [3][nk][nj][ni] is formed on the device."""
+    import torch
+    if nk % 2:
+        raise ValueError("jet grid needs an even azimuthal point count")
+    x = stretched_coordinate(ni, length, 4.0, 0.0, 5.0) if axial_stretch else np.linspace(0.0, length, ni)
+    r = stretched_coordinate(nj, radius, radial_ratio, 0.5, 0.5)
+    th = 2.0 * math.pi * np.arange(nk) / nk
+    xt = torch.as_tensor(x, dtype=torch.float64, device=device)
+    rt = torch.as_tensor(r, dtype=torch.float64, device=device)
+    ct = torch.as_tensor(np.cos(th), dtype=torch.float64, device=device)
+    st = torch.as_tensor(np.sin(th), dtype=torch.float64, device=device)
+    xyz = torch.empty((3, nk, nj, ni), dtype=torch.float64, device=device)
+    xyz[0] = xt[None, None, :]
+    xyz[1] = (ct[:, None] * rt[None, :])[:, :, None]
+    xyz[2] = (st[:, None] * rt[None, :])[:, :, None]
+    return xyz
+
+
+def jet_state_device(xyz, jet_mach: float = 1.4, theta_mom: float = 0.05, gamma: float = GAMMA):
+    """jet_state on a torch device: parallel tanh jet, uniform rho and p."""
+    import torch
+    r = torch.sqrt(xyz[1] * xyz[1] + xyz[2] * xyz[2])
+    u = 0.5 * jet_mach * (1.0 + torch.tanh((0.5 - r) / (2.0 * theta_mom)))
+    q = torch.zeros((5,) + tuple(r.shape), dtype=torch.float64, device=xyz.device)
+    q[0] = 1.0
+    q[1] = u
+    q[4] = (1.0 / gamma) / (gamma - 1.0) + 0.5 * u * u
+    return q
+
+
+# Paper's Table "mesh" (axial x radial points; 361 azimuthal points with the first and
+# last superposed -> 360 unique).
+PAPER_MESHES = {"A": (128, 128), "B": (256, 128), "C": (256, 256), "D": (512, 256), "E": (512, 512),
+                "F": (1024, 512), "G": (1024, 1024), "H": (2048, 1024), "I": (1700, 1700)}
+
+
 # ---------------------------------------------------------------------------
 # Initial states (conserved variables [rho, rho u, rho v, rho w, e])
 # ---------------------------------------------------------------------------
