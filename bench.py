@@ -248,6 +248,8 @@ def main():
     torch.cuda.set_device(local)
     build.build()
     jz.load()
+    if args.paper_meshes:
+        return run_paper_meshes(args, jz, W, torch)
 
     g, q, prm = W.make_workload(args.workload)
     npts = g.npts
@@ -287,9 +289,6 @@ def main():
         final = torch.empty_like(q_dev)
         solver.get_state(final)
         return solver, dict(ms=t_max, prof=prof, clocks=clocks, stats=stats, final=final)
-
-    if args.paper_meshes:
-        return run_paper_meshes(args, jz, W, torch)
 
     if args.fp32_only:
         solver32, r32 = timed_form(jz.JZ_PREC_FP32FLUX, True)
