@@ -696,6 +696,51 @@ def functional_gradient(grid: Grid, Q0, c: Consts, amps, nsteps: int, dt, obs: O
     return J.detach(), g
 
 
+# ---------------------------------------------------------------------------
+# Flow statistics (Sec. "Validation": time-averaged axial velocity on the
+# centreline and in radial profiles at fixed x/D, rms of the axial velocity,
+# potential-core length where the centreline mean drops to 95% of U_j)
+# ---------------------------------------------------------------------------
+def flow_statistics(samples):
+    """Time statistics of the axial velocity u_x = (rho u_x) / rho over a list of states
+    Q [5][nk][nj][ni]: per node the mean and the rms about it (population definitions,
+    two passes), each then averaged over the azimuth k.  Returns (mean, rms), [nj][ni]."""
+    U = torch.stack([Q[1] / Q[0] for Q in samples])            # [S][nk][nj][ni]
+    mean = U.mean(dim=0)
+    rms = torch.sqrt(((U - mean) ** 2).mean(dim=0))
+    return mean.mean(dim=0), rms.mean(dim=0)
+
+
+def station_profile(field, x, x0: float):
+    """Radial profile of field [nj][ni] at axial position x0: linear interpolation in x
+    between the two i lines that bracket x0 (x [ni] increasing)."""
+    x = torch.as_tensor(x, dtype=DT)
+    if not (float(x[0]) <= x0 <= float(x[-1])):
+        raise ValueError("station outside the axial range")
+    i1 = int((x >= x0).nonzero().flatten()[0])
+    if i1 == 0:
+        return field[:, 0].clone()
+    i0 = i1 - 1
+    w = (x0 - x[i0]) / (x[i1] - x[i0])
+    return (1.0 - w) * field[:, i0] + w * field[:, i1]
+
+
+def potential_core_length(axis_mean, x, u_jet: float, frac: float = 0.95):
+    """First axial position where the centreline mean velocity axis_mean [ni] falls below
+    frac * u_jet, interpolated linearly between the bracketing i lines; None if it never does."""
+    x = torch.as_tensor(x, dtype=DT)
+    thr = frac * u_jet
+    below = (axis_mean < thr).nonzero().flatten()
+    if below.numel() == 0:
+        return None
+    i1 = int(below[0])
+    if i1 == 0:
+        return float(x[0])
+    i0 = i1 - 1
+    w = (axis_mean[i0] - thr) / (axis_mean[i0] - axis_mean[i1])
+    return float(x[i0] + w * (x[i1] - x[i0]))
+
+
 def make(xyz, ni, nj, nk, topology, period, prm):
     """Convenience: (Grid, Consts) from plain arrays and a parameter object."""
     return Grid(ni, nj, nk, xyz, topology, period), Consts(prm)

@@ -541,3 +541,48 @@ def test_functional_reverse_sweep_matches_central_differences():
         fd = (Jp - Jm) / (2 * h)
         ad = (gr * d).sum().item()
         assert abs(fd - ad) <= 1e-6 * gr.abs().max().item(), (kind, fd, ad)
+
+
+def test_flow_statistics_closed_form():
+    """u_x = a + b sin(2 pi s / S) over S samples of a full period: the time mean is a and
+    the rms is |b| / sqrt(2) exactly, per node; rho varies, so u_x must be (rho u_x) / rho.
+    The azimuthal average runs over k only."""
+    nk, nj, ni, S = 6, 5, 7, 8
+    rng = np.random.Generator(np.random.PCG64(3))
+    a = torch.as_tensor(rng.uniform(0.2, 1.4, (nk, nj, ni)))
+    b = torch.as_tensor(rng.uniform(-0.1, 0.1, (nk, nj, ni)))
+    samples = []
+    for s in range(S):
+        rho = 1.0 + 0.2 * torch.as_tensor(rng.uniform(-1, 1, (nk, nj, ni)))
+        u = a + b * math.sin(2 * math.pi * s / S)
+        Q = torch.zeros((5, nk, nj, ni), dtype=torch.float64)
+        Q[0] = rho
+        Q[1] = rho * u
+        Q[2] = rho * 0.3
+        Q[4] = 2.0
+        samples.append(Q)
+    mean, rms = O.flow_statistics(samples)
+    assert mean.shape == (nj, ni) and rms.shape == (nj, ni)
+    assert torch.allclose(mean, a.mean(0), rtol=0, atol=1e-14)
+    assert torch.allclose(rms, (b.abs() / math.sqrt(2.0)).mean(0), rtol=0, atol=1e-14)
+
+
+def test_station_profile_and_potential_core():
+    """Interpolation in x is exact for a field linear in x (non-uniform x, station between
+    and on grid lines); the potential core ends where a piecewise-linear centreline
+    profile crosses 0.95 U_j, exactly, and is None when it never does."""
+    x = torch.as_tensor(np.cumsum(np.r_[0.0, np.random.Generator(np.random.PCG64(5)).uniform(0.2, 0.9, 20)]))
+    nj = 4
+    f = torch.stack([1.0 + (j + 1) * 0.5 * x for j in range(nj)])          # [nj][ni]
+    for x0 in (float(x[3]), 0.5 * float(x[7] + x[8]), float(x[-1]), float(x[0])):
+        prof = O.station_profile(f, x, x0)
+        assert torch.allclose(prof, torch.tensor([1.0 + (j + 1) * 0.5 * x0 for j in range(nj)], dtype=torch.float64),
+                              rtol=0, atol=1e-13)
+    with pytest.raises(ValueError):
+        O.station_profile(f, x, float(x[-1]) + 1.0)
+    uj, xc, slope = 1.4, float(x[6]), 0.02
+    axis = torch.where(x <= xc, torch.full_like(x, uj), uj * (1.0 - slope * (x - xc)))
+    expect = xc + 0.05 / slope
+    assert float(x[0]) < expect < float(x[-1])
+    assert abs(O.potential_core_length(axis, x, uj) - expect) < 1e-12
+    assert O.potential_core_length(torch.full_like(x, uj), x, uj) is None
