@@ -204,6 +204,41 @@ int jz_profile_read(jz_solver* s, double* ms, long long* launches);
 /* Short name of a kernel kind ("" if out of range). */
 const char* jz_profile_name(int kind);
 
+/* ---- snapshots (checkpoint / restart) ------------------------------------ *
+ * The paper restarts long runs from stored solution files (Algorithm 2
+ * starts from an initial condition or a restart file; Sec. "Parallel I/O"
+ * writes them per rank through CGNS/HDF5).  Here one GPU holds the whole
+ * grid, so a snapshot is one raw binary file written from the host:
+ *
+ *   header, 256 bytes, little-endian:
+ *     char     magic[8]  = "JZSNAP01"
+ *     int32    version = 1, header_bytes = 256
+ *     int32    ni, nj, nk, topology, precision, flags (bit 0: rate valid)
+ *     int64    steps                 steps taken since jz_set_state
+ *     float64  t, dt, rate, res_sum  time, last time step, CFL rate of Q^n
+ *                                    (valid if flags bit 0), last residual sum
+ *     uint64   params_hash           FNV-1a 64 of the jz_params fields
+ *     uint64   data_hash             FNV-1a 64 over the data's 64-bit words
+ *     zero padding to 256 bytes
+ *   data: Q^n as [5][nk][nj][ni] float64, i fastest (the jz_get_state layout).
+ *
+ * jz_save_snapshot writes the solver's Q^n, time, step count and the CFL
+ * rate the next step would use (FP32-flux form), so that continuing from
+ * jz_load_snapshot reproduces an uninterrupted run bit for bit.
+ * jz_load_snapshot requires the same grid shape and topology and the same
+ * parameters (params_hash); the rate is restored only when the precision
+ * matches, otherwise the next step reduces it afresh.  The file is created
+ * or truncated by save; `path` is a NUL-terminated file name.
+ * Both calls synchronise the solver's stream and allocate a device staging
+ * buffer [5][N] (kept by the solver) and 2 x 64 MiB of pinned host memory
+ * (freed on return).
+ * Errors: JZ_ERR_ARG (NULL arguments, unreadable/unwritable file, bad magic
+ * or version, shape/topology/parameter mismatch, short file, data hash
+ * mismatch), JZ_ERR_STATE (save without a state), JZ_ERR_OOM, JZ_ERR_CUDA. */
+#define JZ_SNAPSHOT_HEADER_BYTES 256
+int jz_save_snapshot(jz_solver* s, const char* path);
+int jz_load_snapshot(jz_solver* s, const char* path);
+
 /* ---- allocation-free residual ------------------------------------------- *
  * The paper has no counterpart to this entry point; it is a service for
  * callers that cannot have the library allocate device memory: code whose

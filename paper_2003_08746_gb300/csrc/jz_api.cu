@@ -3,6 +3,8 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdarg>
+#include <cstddef>
+#include <cstdint>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -728,3 +730,147 @@ const char* jz_profile_name(int kind) {
 }
 
 }  // extern "C"
+
+// ---- snapshots ---------------------------------------------------------------------
+namespace {
+
+constexpr char kSnapMagic[8] = {'J', 'Z', 'S', 'N', 'A', 'P', '0', '1'};
+constexpr size_t kSnapChunk = 64u << 20;        // bytes per host transfer
+
+struct SnapHeader {
+  char magic[8];
+  int32_t version, header_bytes;
+  int32_t ni, nj, nk, topology, precision, flags;
+  int64_t steps;
+  double t, dt, rate, res_sum;
+  uint64_t params_hash, data_hash;
+  unsigned char pad[JZ_SNAPSHOT_HEADER_BYTES - 8 - 8 * 4 - 8 - 4 * 8 - 2 * 8];
+};
+static_assert(sizeof(SnapHeader) == JZ_SNAPSHOT_HEADER_BYTES, "snapshot header size");
+
+constexpr uint64_t kFnvOffset = 1469598103934665603ull, kFnvPrime = 1099511628211ull;
+
+// FNV-1a over 64-bit words (one step per word).
+uint64_t fnv_words(uint64_t h, const void* p, size_t nwords) {
+  const unsigned char* b = static_cast<const unsigned char*>(p);
+  for (size_t i = 0; i < nwords; ++i) {
+    uint64_t w;
+    std::memcpy(&w, b + 8 * i, 8);
+    h = (h ^ w) * kFnvPrime;
+  }
+  return h;
+}
+
+// The parameters that fix a step's result: every jz_params field except precision.
+uint64_t params_hash(const jz_params& p) {
+  return fnv_words(kFnvOffset, &p, offsetof(jz_params, precision) / sizeof(double));
+}
+
+struct FileCloser {
+  FILE* f = nullptr;
+  ~FileCloser() { if (f) std::fclose(f); }
+};
+struct PinnedHost {
+  void* p = nullptr;
+  ~PinnedHost() { if (p) cudaFreeHost(p); }
+};
+
+}  // namespace
+
+int jz_save_snapshot(jz_solver* s, const char* path) {
+  if (!s || !path) return fail(JZ_ERR_ARG, "jz_save_snapshot: NULL argument");
+  if (!s->has_state) return fail(JZ_ERR_STATE, "jz_save_snapshot: no state set");
+  const jz::Dims& d = s->grid->d;
+  int r = ensure_staging(s);
+  if (r) return r;
+  JZ_CK(jz::unpack_real(d, s->qn.q, s->staging, 5, s->st));
+  jz::Scalars h;
+  JZ_CK(cudaMemcpyAsync(&h, s->sc, sizeof h, cudaMemcpyDeviceToHost, s->st));
+  JZ_CK(cudaStreamSynchronize(s->st));
+  SnapHeader hd;
+  std::memset(&hd, 0, sizeof hd);
+  std::memcpy(hd.magic, kSnapMagic, 8);
+  hd.version = 1;
+  hd.header_bytes = JZ_SNAPSHOT_HEADER_BYTES;
+  hd.ni = d.ni; hd.nj = d.nj; hd.nk = d.nk; hd.topology = d.topo;
+  hd.precision = s->prm.precision;
+  hd.flags = s->rate_ready ? 1 : 0;
+  hd.steps = s->steps;
+  hd.t = h.t; hd.dt = h.dt; hd.rate = h.rate_max; hd.res_sum = h.res_sum;
+  hd.params_hash = params_hash(s->prm);
+  FileCloser fc;
+  fc.f = std::fopen(path, "wb");
+  if (!fc.f) return fail(JZ_ERR_ARG, "jz_save_snapshot: cannot open '%s' for writing", path);
+  // header first (data hash patched in at the end)
+  if (std::fwrite(&hd, sizeof hd, 1, fc.f) != 1) return fail(JZ_ERR_ARG, "jz_save_snapshot: write failed");
+  PinnedHost buf;
+  JZ_CK(cudaMallocHost(&buf.p, 2 * kSnapChunk));
+  const size_t total = 5 * sizeof(double) * (size_t)npts(d);
+  const char* src = reinterpret_cast<const char*>(s->staging);
+  uint64_t dh = kFnvOffset;
+  for (size_t off = 0; off < total; off += kSnapChunk) {
+    const size_t n = std::min(kSnapChunk, total - off);
+    char* hb = static_cast<char*>(buf.p) + ((off / kSnapChunk) & 1) * kSnapChunk;
+    JZ_CK(cudaMemcpyAsync(hb, src + off, n, cudaMemcpyDeviceToHost, s->st));
+    JZ_CK(cudaStreamSynchronize(s->st));
+    dh = fnv_words(dh, hb, n / 8);
+    if (std::fwrite(hb, 1, n, fc.f) != n) return fail(JZ_ERR_ARG, "jz_save_snapshot: write failed");
+  }
+  hd.data_hash = dh;
+  if (std::fseek(fc.f, 0, SEEK_SET) != 0 || std::fwrite(&hd, sizeof hd, 1, fc.f) != 1)
+    return fail(JZ_ERR_ARG, "jz_save_snapshot: header rewrite failed");
+  const int cerr = std::fclose(fc.f);
+  fc.f = nullptr;
+  if (cerr != 0) return fail(JZ_ERR_ARG, "jz_save_snapshot: close failed");
+  return JZ_OK;
+}
+
+int jz_load_snapshot(jz_solver* s, const char* path) {
+  if (!s || !path) return fail(JZ_ERR_ARG, "jz_load_snapshot: NULL argument");
+  const jz::Dims& d = s->grid->d;
+  FileCloser fc;
+  fc.f = std::fopen(path, "rb");
+  if (!fc.f) return fail(JZ_ERR_ARG, "jz_load_snapshot: cannot open '%s'", path);
+  SnapHeader hd;
+  if (std::fread(&hd, sizeof hd, 1, fc.f) != 1) return fail(JZ_ERR_ARG, "jz_load_snapshot: short header");
+  if (std::memcmp(hd.magic, kSnapMagic, 8) != 0 || hd.version != 1 || hd.header_bytes != JZ_SNAPSHOT_HEADER_BYTES)
+    return fail(JZ_ERR_ARG, "jz_load_snapshot: '%s' is not a version-1 snapshot", path);
+  if (hd.ni != d.ni || hd.nj != d.nj || hd.nk != d.nk || hd.topology != d.topo)
+    return fail(JZ_ERR_ARG, "jz_load_snapshot: snapshot grid %d x %d x %d (topology %d) does not match %d x %d x %d (%d)",
+                hd.ni, hd.nj, hd.nk, hd.topology, d.ni, d.nj, d.nk, d.topo);
+  if (hd.params_hash != params_hash(s->prm))
+    return fail(JZ_ERR_ARG, "jz_load_snapshot: snapshot was written with different parameters");
+  int r = ensure_staging(s);
+  if (r) return r;
+  PinnedHost buf;
+  JZ_CK(cudaMallocHost(&buf.p, 2 * kSnapChunk));
+  const size_t total = 5 * sizeof(double) * (size_t)npts(d);
+  char* dst = reinterpret_cast<char*>(s->staging);
+  uint64_t dh = kFnvOffset;
+  for (size_t off = 0; off < total; off += kSnapChunk) {
+    const size_t n = std::min(kSnapChunk, total - off);
+    char* hb = static_cast<char*>(buf.p) + ((off / kSnapChunk) & 1) * kSnapChunk;
+    // the copy queued from this half two chunks ago must be done before it is refilled
+    JZ_CK(cudaStreamSynchronize(s->st));
+    if (std::fread(hb, 1, n, fc.f) != n) return fail(JZ_ERR_ARG, "jz_load_snapshot: short file '%s'", path);
+    dh = fnv_words(dh, hb, n / 8);
+    JZ_CK(cudaMemcpyAsync(dst + off, hb, n, cudaMemcpyHostToDevice, s->st));
+  }
+  JZ_CK(cudaStreamSynchronize(s->st));
+  if (dh != hd.data_hash) return fail(JZ_ERR_ARG, "jz_load_snapshot: data hash mismatch in '%s'", path);
+  r = load_state(s, s->staging, s->qn);
+  if (r) return r;
+  jz::Scalars h;
+  std::memset(&h, 0, sizeof h);
+  h.t = hd.t;
+  h.dt = hd.dt;
+  h.res_sum = hd.res_sum;
+  const bool rate_ok = (hd.flags & 1) && hd.precision == s->prm.precision;
+  if (rate_ok) h.rate_max = hd.rate;
+  JZ_CK(cudaMemcpyAsync(s->sc, &h, sizeof h, cudaMemcpyHostToDevice, s->st));
+  JZ_CK(cudaStreamSynchronize(s->st));
+  s->steps = hd.steps;
+  s->rate_ready = rate_ok;
+  s->has_state = true;
+  return JZ_OK;
+}

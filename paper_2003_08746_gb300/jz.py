@@ -27,7 +27,7 @@ N_MODES, N_FREQ = 8, 4
 EXPORTS = ("jz_last_error", "jz_version", "jz_create_grid", "jz_destroy_grid", "jz_compute_metrics",
            "jz_get_metrics", "jz_create", "jz_destroy", "jz_set_state", "jz_get_state", "jz_residual",
            "jz_rk_step", "jz_profile", "jz_profile_read", "jz_profile_name", "jz_residual_noalloc",
-           "jz_adjoint_step")
+           "jz_adjoint_step", "jz_save_snapshot", "jz_load_snapshot")
 JZ_NOALLOC_SCRATCH_BYTES = 64 * 1024 * 1024
 JZ_NPROF = 9
 
@@ -86,6 +86,8 @@ def load(path: str | None = None) -> ctypes.CDLL:
         "jz_profile_name": ([i], ctypes.c_char_p),
         "jz_residual_noalloc": ([vp, ctypes.POINTER(jz_params), vp, vp, vp], i),
         "jz_adjoint_step": ([vp, vp, i, i, d, ctypes.POINTER(ctypes.c_double), vp], i),
+        "jz_save_snapshot": ([vp, ctypes.c_char_p], i),
+        "jz_load_snapshot": ([vp, ctypes.c_char_p], i),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -180,6 +182,41 @@ def jz_residual_noalloc(grid_h, params: jz_params, q, rhs, stream=None):
     """Residual with the library's fixed scratch array (no device allocation); device q and rhs."""
     st = ctypes.c_void_p(0 if stream is None else int(stream))
     _check(load().jz_residual_noalloc(grid_h, ctypes.byref(params), _ptr(q), _ptr(rhs), st))
+
+
+def jz_save_snapshot(h, path) -> None:
+    _check(load().jz_save_snapshot(h, os.fsencode(path)))
+
+
+def jz_load_snapshot(h, path) -> None:
+    _check(load().jz_load_snapshot(h, os.fsencode(path)))
+
+
+SNAPSHOT_HEADER_BYTES = 256
+_SNAP_FIELDS = np.dtype([("magic", "S8"), ("version", "<i4"), ("header_bytes", "<i4"), ("ni", "<i4"),
+                         ("nj", "<i4"), ("nk", "<i4"), ("topology", "<i4"), ("precision", "<i4"),
+                         ("flags", "<i4"), ("steps", "<i8"), ("t", "<f8"), ("dt", "<f8"), ("rate", "<f8"),
+                         ("res_sum", "<f8"), ("params_hash", "<u8"), ("data_hash", "<u8")])
+
+
+def read_snapshot(path):
+    """Parse a snapshot file on the host (no GPU): (header dict, Q^n as [5][nk][nj][ni] float64).
+
+    File layout (as written by jz_save_snapshot): a 256-byte little-endian header, then
+    Q^n in the jz_get_state layout."""
+    with open(path, "rb") as f:
+        raw = f.read(SNAPSHOT_HEADER_BYTES)
+        if len(raw) != SNAPSHOT_HEADER_BYTES:
+            raise ValueError("short snapshot header")
+        hd = np.frombuffer(raw[:_SNAP_FIELDS.itemsize], dtype=_SNAP_FIELDS)[0]
+        head = {k: (hd[k].item() if k != "magic" else bytes(hd[k])) for k in _SNAP_FIELDS.names}
+        if head["magic"] != b"JZSNAP01" or head["version"] != 1:
+            raise ValueError("not a version-1 jz snapshot")
+        n = 5 * head["ni"] * head["nj"] * head["nk"]
+        q = np.fromfile(f, dtype="<f8", count=n)
+    if q.size != n:
+        raise ValueError("short snapshot data")
+    return head, q.reshape(5, head["nk"], head["nj"], head["ni"])
 
 
 def jz_rk_step(h, nsteps: int, want_stats: bool = True):
@@ -296,6 +333,12 @@ class Solver:
 
     def step(self, nsteps: int = 1, stats: bool = True):
         return jz_rk_step(self.h, nsteps, stats)
+
+    def save(self, path):
+        jz_save_snapshot(self.h, path)
+
+    def load(self, path):
+        jz_load_snapshot(self.h, path)
 
     def profile(self, enable: bool = True):
         jz_profile(self.h, enable)

@@ -4,6 +4,8 @@ import ctypes
 import os
 import re
 
+import numpy as np
+
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -78,3 +80,25 @@ def test_product_path_has_no_oracle_import():
             if fn.endswith((".py", ".cu", ".cuh", ".h")):
                 src = open(os.path.join(dirpath, fn)).read()
                 assert "from oracle" not in src and "import oracle" not in src
+
+
+def test_snapshot_reader_layout(tmp_path):
+    """read_snapshot parses the documented layout: 256-byte little-endian header, then
+    Q^n as [5][nk][nj][ni] float64 (file written here field by field)."""
+    import struct
+    from paper_2003_08746_gb300 import jz
+    ni, nj, nk = 5, 4, 6
+    q = np.random.default_rng(0).standard_normal((5, nk, nj, ni))
+    head = b"JZSNAP01" + struct.pack("<8i", 1, 256, ni, nj, nk, 2, 1, 1) + struct.pack("<q", 17)
+    head += struct.pack("<4d", 0.25, 1e-3, 3.5, 0.0) + struct.pack("<2Q", 11, 22)
+    head += bytes(256 - len(head))
+    assert len(head) == 256
+    p = tmp_path / "s.bin"
+    p.write_bytes(head + q.astype("<f8").tobytes())
+    hd, qr = jz.read_snapshot(p)
+    assert (hd["ni"], hd["nj"], hd["nk"], hd["topology"], hd["precision"], hd["flags"]) == (ni, nj, nk, 2, 1, 1)
+    assert hd["steps"] == 17 and hd["t"] == 0.25 and hd["dt"] == 1e-3 and hd["params_hash"] == 11
+    assert np.array_equal(qr, q)
+    p.write_bytes(head + q.astype("<f8").tobytes()[:-8])
+    with pytest.raises(ValueError, match="short"):
+        jz.read_snapshot(p)
