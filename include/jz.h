@@ -188,7 +188,8 @@ int jz_adjoint_step(jz_solver* s, const double* forcing_amps, int nsteps, int ck
 #define JZ_PROF_REDUCE   6   /* CFL, time, statistics reductions                           */
 #define JZ_PROF_FUSED32  7   /* fused FP32-flux stage kernel                               */
 #define JZ_PROF_ADJOINT  8   /* adjoint stage kernels                                      */
-#define JZ_NPROF         9
+#define JZ_PROF_STATS    9   /* flow-statistics sampling                                   */
+#define JZ_NPROF         10
 
 /* Turn per-kernel timing on or off.  While on, the solver records a CUDA
  * event on its stream after every kernel it launches (intervals between
@@ -203,6 +204,46 @@ int jz_profile_read(jz_solver* s, double* ms, long long* launches);
 
 /* Short name of a kernel kind ("" if out of range). */
 const char* jz_profile_name(int kind);
+
+/* ---- flow statistics ------------------------------------------------------ *
+ * The paper validates the jet against measurements through time statistics
+ * of the axial velocity (Sec. "Validation": mean axial velocity along the
+ * centreline and radial profiles at x/D = 2.5 and 5, axial-velocity rms,
+ * potential-core length).  The library accumulates them on the GPU:
+ *
+ *   u = (rho u_x) / rho at every real node, sampled from Q^n;
+ *   per node: time mean  m = (1/S) sum_s u_s  and  rms = sqrt((1/S) sum_s (u_s - m)^2)
+ *   (population definitions, accumulated with Welford's update);
+ *   read-out: both averaged over the azimuth k, giving [nj][ni] arrays.
+ *
+ * jz_stats_begin allocates 2 x N accumulators plus 2 x ni x nj outputs
+ * (device, owned by the solver), zeroes them, and makes jz_rk_step add a
+ * sample after every `every`-th step (steps counted since jz_set_state or
+ * the snapshot; every = 0: samples only through jz_stats_sample).  Calling
+ * it again restarts the statistics.  jz_stats_sample adds Q^n now.
+ * jz_stats_read writes mean and rms ([nj][ni], i fastest; host or device
+ * pointers, either may be NULL) and the sample count (may be NULL); it
+ * synchronises the stream when a pointer is on the host.  jz_stats_end
+ * frees the accumulators (also freed by jz_destroy).
+ * Errors: JZ_ERR_ARG (NULL solver, every < 0, nj or nk above 65535),
+ * JZ_ERR_STATE (no state set; read/sample before begin; read with no
+ * sample), JZ_ERR_OOM, JZ_ERR_CUDA. */
+int jz_stats_begin(jz_solver* s, int every);
+int jz_stats_sample(jz_solver* s);
+int jz_stats_read(jz_solver* s, double* mean, double* rms, long long* nsamples);
+int jz_stats_end(jz_solver* s);
+
+/* Host-only helpers for the statistics' stations (no GPU involved):
+ * jz_station_profile: the column profile of field [nj][ni] (i fastest) at
+ * axial position x0, linearly interpolated in x between the two i lines
+ * that bracket it (x [ni] strictly increasing; x0 = x[i] returns column i
+ * exactly); out [nj].  JZ_ERR_ARG if x0 lies outside [x[0], x[ni-1]].
+ * jz_potential_core: the first axial position where the centreline mean
+ * axis [ni] drops below frac * u_jet (the paper uses 95% of U_j),
+ * interpolated linearly between the bracketing i lines; NaN if it never
+ * drops.  Both return JZ_ERR_ARG on NULL pointers or ni < 2. */
+int jz_station_profile(const double* field, const double* x, int ni, int nj, double x0, double* out);
+int jz_potential_core(const double* axis, const double* x, int ni, double u_jet, double frac, double* x_core);
 
 /* ---- snapshots (checkpoint / restart) ------------------------------------ *
  * The paper restarts long runs from stored solution files (Algorithm 2

@@ -87,6 +87,12 @@ struct jz_solver {
   jz::Inflow in;
   double* part = nullptr;
   double* staging = nullptr;      // [5][N], allocated on first host transfer
+  // flow statistics (jz_stats_*): per-node mean and M2, outputs [2][nj][ni]
+  double* fs_mean = nullptr;
+  double* fs_m2 = nullptr;
+  double* fs_out = nullptr;
+  long long fs_n = 0;
+  int fs_every = 0;
   long long steps = 0;
   long long n_adv = 0;
   bool has_state = false;
@@ -98,7 +104,16 @@ struct jz_solver {
   double prof_ms[JZ_NPROF] = {0};
   long long launches[JZ_NPROF] = {0};
   DevMem mem;
+  void free_stats() {
+    if (fs_mean) cudaFree(fs_mean);
+    if (fs_m2) cudaFree(fs_m2);
+    if (fs_out) cudaFree(fs_out);
+    fs_mean = fs_m2 = fs_out = nullptr;
+    fs_n = 0;
+    fs_every = 0;
+  }
   ~jz_solver() {
+    free_stats();
     for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
     for (cudaEvent_t e : ev_marks) cudaEventDestroy(e);
   }
@@ -206,6 +221,12 @@ int run_step(jz_solver* s) {
   JZ_RUN(JZ_PROF_REDUCE, jz::set_dt(s->c, s->sc, 1, s->st));
   s->steps += 1;
   s->rate_ready = s->fp32 && s->c.dt_fixed <= 0.0;
+  return JZ_OK;
+}
+
+int stats_sample(jz_solver* s) {
+  s->fs_n += 1;
+  JZ_RUN(JZ_PROF_STATS, jz::flow_sample(s->grid->d, s->qn, s->fs_mean, s->fs_m2, s->fs_n, s->st));
   return JZ_OK;
 }
 
@@ -536,6 +557,10 @@ int jz_rk_step(jz_solver* s, int nsteps, jz_step_stats* out) {
   for (int n = 0; n < nsteps; ++n) {
     int r = run_step(s);
     if (r) return r;
+    if (s->fs_every > 0 && s->steps % s->fs_every == 0) {
+      r = stats_sample(s);
+      if (r) return r;
+    }
   }
   if (!out) return JZ_OK;
   const jz::Dims& d = s->grid->d;
@@ -725,7 +750,7 @@ int jz_profile_read(jz_solver* s, double* ms, long long* launches) {
 
 const char* jz_profile_name(int kind) {
   static const char* names[JZ_NPROF] = {"nodal", "viscous", "faces", "update", "bc", "ghost", "reduce",
-                                        "fused32", "adjoint"};
+                                        "fused32", "adjoint", "stats"};
   return (kind >= 0 && kind < JZ_NPROF) ? names[kind] : "";
 }
 
@@ -874,3 +899,98 @@ int jz_load_snapshot(jz_solver* s, const char* path) {
   s->has_state = true;
   return JZ_OK;
 }
+
+// ---- flow statistics -------------------------------------------------------------
+extern "C" {
+
+int jz_stats_begin(jz_solver* s, int every) {
+  if (!s) return fail(JZ_ERR_ARG, "jz_stats_begin: NULL solver");
+  if (every < 0) return fail(JZ_ERR_ARG, "jz_stats_begin: every < 0");
+  const jz::Dims& d = s->grid->d;
+  if (d.nj > 65535 || d.nk > 65535) return fail(JZ_ERR_ARG, "jz_stats_begin: nj and nk must be <= 65535");
+  s->free_stats();
+  const size_t N = (size_t)npts(d), P = (size_t)d.ni * d.nj;
+  cudaError_t e = cudaMalloc(&s->fs_mean, N * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&s->fs_m2, N * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&s->fs_out, 2 * P * sizeof(double));
+  if (e != cudaSuccess) {
+    s->free_stats();
+    return fail(JZ_ERR_OOM, "jz_stats_begin: %s", cudaGetErrorString(e));
+  }
+  JZ_CK(cudaMemsetAsync(s->fs_mean, 0, N * sizeof(double), s->st));
+  JZ_CK(cudaMemsetAsync(s->fs_m2, 0, N * sizeof(double), s->st));
+  s->fs_every = every;
+  return JZ_OK;
+}
+
+int jz_stats_sample(jz_solver* s) {
+  if (!s) return fail(JZ_ERR_ARG, "jz_stats_sample: NULL solver");
+  if (!s->fs_mean) return fail(JZ_ERR_STATE, "jz_stats_sample: call jz_stats_begin first");
+  if (!s->has_state) return fail(JZ_ERR_STATE, "jz_stats_sample: no state set");
+  return stats_sample(s);
+}
+
+int jz_stats_read(jz_solver* s, double* mean, double* rms, long long* nsamples) {
+  if (!s) return fail(JZ_ERR_ARG, "jz_stats_read: NULL solver");
+  if (!s->fs_mean) return fail(JZ_ERR_STATE, "jz_stats_read: call jz_stats_begin first");
+  if (nsamples) *nsamples = s->fs_n;
+  if (!mean && !rms) return JZ_OK;
+  if (s->fs_n == 0) return fail(JZ_ERR_STATE, "jz_stats_read: no sample taken");
+  const jz::Dims& d = s->grid->d;
+  const size_t P = (size_t)d.ni * d.nj;
+  JZ_RUN(JZ_PROF_STATS, jz::flow_final(d, s->fs_mean, s->fs_m2, s->fs_n, s->fs_out, s->fs_out + P, s->st));
+  double* outs[2] = {mean, rms};
+  bool host = false;
+  for (int a = 0; a < 2; ++a) {
+    if (!outs[a]) continue;
+    const bool dev = is_device_ptr(outs[a]);
+    host = host || !dev;
+    JZ_CK(cudaMemcpyAsync(outs[a], s->fs_out + a * P, P * sizeof(double),
+                          dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s->st));
+  }
+  if (host) JZ_CK(cudaStreamSynchronize(s->st));
+  return JZ_OK;
+}
+
+int jz_stats_end(jz_solver* s) {
+  if (!s) return fail(JZ_ERR_ARG, "jz_stats_end: NULL solver");
+  JZ_CK(cudaStreamSynchronize(s->st));
+  s->free_stats();
+  return JZ_OK;
+}
+
+int jz_station_profile(const double* field, const double* x, int ni, int nj, double x0, double* out) {
+  if (!field || !x || !out || ni < 2 || nj < 1) return fail(JZ_ERR_ARG, "jz_station_profile: bad argument");
+  if (!(x0 >= x[0] && x0 <= x[ni - 1])) return fail(JZ_ERR_ARG, "jz_station_profile: x0 outside the axial range");
+  int i1 = 0;
+  while (x[i1] < x0) ++i1;
+  if (i1 == 0) {
+    for (int j = 0; j < nj; ++j) out[j] = field[(size_t)j * ni];
+    return JZ_OK;
+  }
+  const int i0 = i1 - 1;
+  const double w = (x0 - x[i0]) / (x[i1] - x[i0]);
+  for (int j = 0; j < nj; ++j)
+    out[j] = (1.0 - w) * field[(size_t)j * ni + i0] + w * field[(size_t)j * ni + i1];
+  return JZ_OK;
+}
+
+int jz_potential_core(const double* axis, const double* x, int ni, double u_jet, double frac, double* x_core) {
+  if (!axis || !x || !x_core || ni < 2) return fail(JZ_ERR_ARG, "jz_potential_core: bad argument");
+  const double thr = frac * u_jet;
+  for (int i = 0; i < ni; ++i) {
+    if (axis[i] < thr) {
+      if (i == 0) {
+        *x_core = x[0];
+      } else {
+        const double w = (axis[i - 1] - thr) / (axis[i - 1] - axis[i]);
+        *x_core = x[i - 1] + w * (x[i] - x[i - 1]);
+      }
+      return JZ_OK;
+    }
+  }
+  *x_core = NAN;
+  return JZ_OK;
+}
+
+}  // extern "C"

@@ -188,6 +188,10 @@ int stat_partial_count();
 cudaError_t stats_with(const Dims& d, const Consts& c, const GridDev& g, const State& q, Scalars* sc,
                        double* part, cudaStream_t st);
 cudaError_t check_volume(const Dims& d, const GridDev& g, int* bad, cudaStream_t st);
+// flow statistics of the axial velocity (jz_stats.cu)
+cudaError_t flow_sample(const Dims& d, const State& q, double* mean, double* m2, long long n, cudaStream_t st);
+cudaError_t flow_final(const Dims& d, const double* mean, const double* m2, long long n, double* out_mean,
+                       double* out_rms, cudaStream_t st);
 
 // adjoint (jz_adjoint.cu)
 cudaError_t adj_update(const Dims& d, const GridDev& g, const Adj64& a, double adt, cudaStream_t st);

@@ -27,9 +27,10 @@ N_MODES, N_FREQ = 8, 4
 EXPORTS = ("jz_last_error", "jz_version", "jz_create_grid", "jz_destroy_grid", "jz_compute_metrics",
            "jz_get_metrics", "jz_create", "jz_destroy", "jz_set_state", "jz_get_state", "jz_residual",
            "jz_rk_step", "jz_profile", "jz_profile_read", "jz_profile_name", "jz_residual_noalloc",
-           "jz_adjoint_step", "jz_save_snapshot", "jz_load_snapshot")
+           "jz_adjoint_step", "jz_save_snapshot", "jz_load_snapshot", "jz_stats_begin", "jz_stats_sample",
+           "jz_stats_read", "jz_stats_end", "jz_station_profile", "jz_potential_core")
 JZ_NOALLOC_SCRATCH_BYTES = 64 * 1024 * 1024
-JZ_NPROF = 9
+JZ_NPROF = 10
 
 
 class JzError(RuntimeError):
@@ -88,6 +89,12 @@ def load(path: str | None = None) -> ctypes.CDLL:
         "jz_adjoint_step": ([vp, vp, i, i, d, ctypes.POINTER(ctypes.c_double), vp], i),
         "jz_save_snapshot": ([vp, ctypes.c_char_p], i),
         "jz_load_snapshot": ([vp, ctypes.c_char_p], i),
+        "jz_stats_begin": ([vp, i], i),
+        "jz_stats_sample": ([vp], i),
+        "jz_stats_read": ([vp, vp, vp, ctypes.POINTER(ctypes.c_longlong)], i),
+        "jz_stats_end": ([vp], i),
+        "jz_station_profile": ([vp, vp, i, i, d, vp], i),
+        "jz_potential_core": ([vp, vp, i, d, d, ctypes.POINTER(ctypes.c_double)], i),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -182,6 +189,49 @@ def jz_residual_noalloc(grid_h, params: jz_params, q, rhs, stream=None):
     """Residual with the library's fixed scratch array (no device allocation); device q and rhs."""
     st = ctypes.c_void_p(0 if stream is None else int(stream))
     _check(load().jz_residual_noalloc(grid_h, ctypes.byref(params), _ptr(q), _ptr(rhs), st))
+
+
+def jz_stats_begin(h, every: int) -> None:
+    _check(load().jz_stats_begin(h, int(every)))
+
+
+def jz_stats_sample(h) -> None:
+    _check(load().jz_stats_sample(h))
+
+
+def jz_stats_read(h, mean=None, rms=None) -> int:
+    """Fill mean and rms ([nj][ni] float64, host or device; None to skip); returns the sample count."""
+    n = ctypes.c_longlong()
+    _check(load().jz_stats_read(h, None if mean is None else _ptr(mean), None if rms is None else _ptr(rms),
+                                ctypes.byref(n)))
+    return n.value
+
+
+def jz_stats_end(h) -> None:
+    _check(load().jz_stats_end(h))
+
+
+def jz_station_profile(field, x, x0: float):
+    """Profile of field [nj][ni] at axial position x0 (x [ni] increasing): array [nj]."""
+    field = np.ascontiguousarray(field, dtype=np.float64)
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    nj, ni = field.shape
+    if x.shape != (ni,):
+        raise ValueError("x must have one entry per i line")
+    out = np.empty(nj)
+    _check(load().jz_station_profile(_ptr(field), _ptr(x), ni, nj, float(x0), _ptr(out)))
+    return out
+
+
+def jz_potential_core(axis, x, u_jet: float, frac: float = 0.95):
+    """First x where axis [ni] falls below frac * u_jet (linear interpolation); None if never."""
+    axis = np.ascontiguousarray(axis, dtype=np.float64)
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    if axis.shape != x.shape:
+        raise ValueError("axis and x must have the same length")
+    xc = ctypes.c_double()
+    _check(load().jz_potential_core(_ptr(axis), _ptr(x), axis.size, float(u_jet), float(frac), ctypes.byref(xc)))
+    return None if np.isnan(xc.value) else xc.value
 
 
 def jz_save_snapshot(h, path) -> None:
@@ -336,6 +386,22 @@ class Solver:
 
     def save(self, path):
         jz_save_snapshot(self.h, path)
+
+    def stats_begin(self, every: int = 1):
+        jz_stats_begin(self.h, every)
+
+    def stats_sample(self):
+        jz_stats_sample(self.h)
+
+    def stats_read(self):
+        """(mean, rms, samples): azimuthally averaged axial-velocity statistics, [nj][ni] each."""
+        mean = np.empty((self.grid.nj, self.grid.ni))
+        rms = np.empty_like(mean)
+        n = jz_stats_read(self.h, mean, rms)
+        return mean, rms, n
+
+    def stats_end(self):
+        jz_stats_end(self.h)
 
     def load(self, path):
         jz_load_snapshot(self.h, path)

@@ -102,3 +102,24 @@ def test_snapshot_reader_layout(tmp_path):
     p.write_bytes(head + q.astype("<f8").tobytes()[:-8])
     with pytest.raises(ValueError, match="short"):
         jz.read_snapshot(p)
+
+
+def test_station_and_core_helpers_vs_oracle():
+    """The library's host-only station and potential-core helpers (no GPU) against the
+    oracle's definitions on random profiles."""
+    import torch
+    from oracle import jz_oracle as O
+    from paper_2003_08746_gb300 import jz
+    rng = np.random.default_rng(4)
+    x = np.cumsum(np.r_[0.0, rng.uniform(0.1, 0.5, 40)])
+    f = rng.standard_normal((9, x.size))
+    for x0 in (x[0], x[5], 0.3 * x[10] + 0.7 * x[11], x[-1], 2.5, 5.0):
+        got = jz.jz_station_profile(f, x, x0)
+        ref = O.station_profile(torch.from_numpy(f), x, float(x0)).numpy()
+        assert np.abs(got - ref).max() <= 1e-15 * np.abs(f).max()
+    with pytest.raises(jz.JzError):
+        jz.jz_station_profile(f, x, x[-1] + 0.1)
+    axis = 1.4 - 0.05 * np.maximum(x - 3.0, 0.0) + 1e-3 * rng.standard_normal(x.size) * (x > 3.0)
+    got, ref = jz.jz_potential_core(axis, x, 1.4), O.potential_core_length(torch.from_numpy(axis), x, 1.4)
+    assert ref is not None and abs(got - ref) <= 1e-13
+    assert jz.jz_potential_core(np.full(x.size, 1.4), x, 1.4) is None
