@@ -48,17 +48,27 @@ bool is_device_ptr(const void* p) {
 // Owner of a list of device allocations.
 struct DevMem {
   std::vector<void*> blocks;
+  cudaStream_t user = nullptr;    // stream whose queued work may still use the blocks
+  bool has_user = false;
   ~DevMem() { release(); }
+  void used_by(cudaStream_t st) {
+    user = st;
+    has_user = true;
+  }
   void release() {
+    if (has_user && !blocks.empty()) cudaStreamSynchronize(user);
     for (void* b : blocks) cudaFree(b);
     blocks.clear();
   }
-  double* alloc(size_t n, cudaError_t& err) {
+  // Zeroed on `st`, the stream that will use the buffer: a plain cudaMemset runs on
+  // the legacy default stream, which a non-blocking stream does not wait for, so a
+  // late memset could wipe data the owner's first kernels had already written.
+  double* alloc(size_t n, cudaError_t& err, cudaStream_t st) {
     void* p = nullptr;
     err = cudaMalloc(&p, n * sizeof(double));
     if (err != cudaSuccess) return nullptr;
     blocks.push_back(p);
-    err = cudaMemset(p, 0, n * sizeof(double));
+    err = cudaMemsetAsync(p, 0, n * sizeof(double), st);
     return static_cast<double*>(p);
   }
 };
@@ -105,6 +115,7 @@ struct jz_solver {
   long long launches[JZ_NPROF] = {0};
   DevMem mem;
   void free_stats() {
+    if (fs_mean || fs_m2 || fs_out) cudaStreamSynchronize(st);   // kernels may still use them
     if (fs_mean) cudaFree(fs_mean);
     if (fs_m2) cudaFree(fs_m2);
     if (fs_out) cudaFree(fs_out);
@@ -126,7 +137,7 @@ long long npts(const jz::Dims& d) { return (long long)d.ni * d.nj * d.nk; }
 int ensure_staging(jz_solver* s) {
   if (s->staging) return JZ_OK;
   cudaError_t e;
-  s->staging = s->mem.alloc(5 * (size_t)npts(s->grid->d), e);
+  s->staging = s->mem.alloc(5 * (size_t)npts(s->grid->d), e, s->st);
   if (!s->staging) return fail(JZ_ERR_OOM, "staging buffer: %s", cudaGetErrorString(e));
   return JZ_OK;
 }
@@ -311,7 +322,7 @@ int jz_create_grid(int ni, int nj, int nk, const double* xyz, const double* peri
                       &g->g.S[3], &g->g.S[4], &g->g.S[5], &g->g.S[6], &g->g.S[7], &g->g.S[8],
                       &g->g.V, &g->g.invV, &g->g.Smag[0], &g->g.Smag[1], &g->g.Smag[2], &g->g.Delta};
   for (double** sl : slots) {
-    *sl = g->mem.alloc(d.Np, e);
+    *sl = g->mem.alloc(d.Np, e, nullptr);
     if (!*sl || e != cudaSuccess) {
       delete g;
       return fail(JZ_ERR_OOM, "grid arrays: %s", cudaGetErrorString(e));
@@ -349,7 +360,7 @@ int jz_compute_metrics(jz_grid* g) {
   double* s9[9];
   cudaError_t e;
   for (int i = 0; i < 9; ++i) {
-    s9[i] = scratch.alloc(d.Np, e);
+    s9[i] = scratch.alloc(d.Np, e, nullptr);
     if (!s9[i]) return fail(JZ_ERR_OOM, "metric scratch: %s", cudaGetErrorString(e));
   }
   int* bad = nullptr;
@@ -409,7 +420,7 @@ int jz_create(jz_grid* g, const jz_params* p, void* stream, jz_solver** out) {
   cudaError_t e = cudaSuccess;
   auto A = [&](double*& dst, size_t n) {
     if (e != cudaSuccess) return;
-    dst = s->mem.alloc(n, e);
+    dst = s->mem.alloc(n, e, s->st);
   };
   for (int m = 0; m < 5; ++m) {
     A(s->qn.q[m], d.Np);
@@ -457,7 +468,7 @@ int jz_create(jz_grid* g, const jz_params* p, void* stream, jz_solver** out) {
     return fail(JZ_ERR_OOM, "jz_create: device allocation failed: %s", cudaGetErrorString(e));
   }
   if (s->fp32) {
-    e = cudaMemcpy(Sf_dev, s->Sf, sizeof(s->Sf), cudaMemcpyHostToDevice);
+    e = cudaMemcpyAsync(Sf_dev, s->Sf, sizeof(s->Sf), cudaMemcpyHostToDevice, s->st);
     if (e == cudaSuccess) e = jz::metrics_to_f32(d, g->g, Sf_dev, s->st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s->st);
     if (e != cudaSuccess) {
@@ -613,12 +624,13 @@ int jz_adjoint_step(jz_solver* s, const double* forcing_amps, int nsteps, int ck
                              : (i == d.ni - 1 ? 0.5 * (x[d.ni - 1] - x[d.ni - 2]) : 0.5 * (x[i + 1] - x[i - 1]));
     w[i] = wr * dx;
   }
-  // device memory for this call
+  // device memory for this call (released after the stream's queued work, also on errors)
   DevMem mem;
+  mem.used_by(s->st);
   cudaError_t e = cudaSuccess;
   auto A = [&](double*& dst, size_t n) {
     if (e != cudaSuccess) return;
-    dst = mem.alloc(n, e);
+    dst = mem.alloc(n, e, s->st);
   };
   auto AS = [&](jz::State& st) {
     for (int m = 0; m < 5; ++m) A(st.q[m], d.Np);
@@ -647,7 +659,7 @@ int jz_adjoint_step(jz_solver* s, const double* forcing_amps, int nsteps, int ck
   for (auto& st : stg) AS(st);
   AS(wa); AS(wb);
   if (e != cudaSuccess) return fail(JZ_ERR_OOM, "jz_adjoint_step: device allocation failed: %s", cudaGetErrorString(e));
-  JZ_CK(cudaMemcpy(wdev, w.data(), sizeof(double) * d.ni, cudaMemcpyHostToDevice));
+  JZ_CK(cudaMemcpyAsync(wdev, w.data(), sizeof(double) * d.ni, cudaMemcpyHostToDevice, s->st));
   // frozen time step and start time
   if (s->c.dt_fixed <= 0.0) JZ_RUN(JZ_PROF_REDUCE, jz::cfl_rate(d, s->c, g, s->qn, s->sc, s->st));
   JZ_RUN(JZ_PROF_REDUCE, jz::set_dt(s->c, s->sc, 0, s->st));

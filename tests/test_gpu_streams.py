@@ -1,0 +1,67 @@
+"""Solvers on a non-blocking stream (a torch side stream) compute exactly what they compute
+on the legacy default stream, also when their device memory is recycled from a solver that
+was just destroyed (the buffers are zeroed on the solver's own stream, so no zeroing can land
+after the solver's first kernels)."""
+import numpy as np
+import pytest
+import torch
+
+from paper_2003_08746_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def jz():
+    from paper_2003_08746_gb300 import build, jz as J
+    build.build()
+    J.load()
+    assert torch.cuda.is_available()
+    return J
+
+
+@pytest.mark.parametrize("prec_name", ["JZ_PREC_FP64", "JZ_PREC_FP32FLUX"])
+def test_side_stream_after_destroy_matches_default_stream(jz, prec_name):
+    prec = getattr(jz, prec_name)
+    g = W.jet_grid(256, 256, 128)
+    q = torch.from_numpy(W.jet_state(g)).cuda()
+    prm = W.jet_params(seed=2)
+    grid = jz.Grid.from_workload(g)
+    ref = jz.Solver(grid, prm, prec)
+    ref.set_state(q, 0.0)
+    st_ref = ref.step(2)
+    q_ref = torch.empty_like(q)
+    ref.get_state(q_ref)
+    torch.cuda.synchronize()
+    for trial in range(2):
+        first = jz.Solver(grid, prm, jz.JZ_PREC_FP64 if trial == 0 else jz.JZ_PREC_FP32FLUX,
+                          stream=torch.cuda.Stream().cuda_stream)
+        first.set_state(q, 0.0)
+        first.step(1, stats=False)
+        first.close()                           # its memory goes back to the driver
+        side = torch.cuda.Stream()
+        s = jz.Solver(grid, prm, prec, stream=side.cuda_stream)
+        s.set_state(q, 0.0)
+        st = s.step(2)
+        out = torch.empty_like(q)
+        s.get_state(out)
+        side.synchronize()
+        assert st.t == st_ref.t and st.min_p == st_ref.min_p
+        assert torch.equal(out, q_ref), f"trial {trial}: max diff {(out - q_ref).abs().max().item()}"
+        s.close()
+
+
+def test_adjoint_on_side_stream(jz):
+    g = W.jet_grid(32, 24, 16)
+    prm = W.jet_params(seed=4)
+    q = W.jet_state(g)
+    grid = jz.Grid.from_workload(g)
+    A = np.asarray(prm.forcing_amp)
+    a = jz.Solver(grid, prm)
+    a.set_state(q, 0.0)
+    Ja, ga = jz.jz_adjoint_step(a.h, A, 6, 3, 0.75)
+    side = torch.cuda.Stream()
+    b = jz.Solver(grid, prm, stream=side.cuda_stream)
+    b.set_state(q, 0.0)
+    Jb, gb = jz.jz_adjoint_step(b.h, A, 6, 3, 0.75)
+    assert Ja == Jb and np.array_equal(ga, gb)
