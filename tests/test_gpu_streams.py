@@ -64,4 +64,6 @@ def test_adjoint_on_side_stream(jz):
     b = jz.Solver(grid, prm, stream=side.cuda_stream)
     b.set_state(q, 0.0)
     Jb, gb = jz.jz_adjoint_step(b.h, A, 6, 3, 0.75)
-    assert Ja == Jb and np.array_equal(ga, gb)
+    # J and dJ/dA are sums with atomic additions: equal up to the order of those sums
+    assert abs(Ja - Jb) <= 1e-12 * abs(Ja)
+    assert np.abs(ga - gb).max() <= 1e-12 * np.abs(ga).max()
