@@ -42,8 +42,8 @@ FP64_PEAK_TFLOPS = 152 * 4 * 2.07e9 / 1e12
 FLOPS_PER_POINT = {"nodal": 83, "viscous": 233, "faces": 168, "update": 76}
 # DRAM bytes per node of a kernel launch from an ncu capture (dram__bytes_read.sum +
 # dram__bytes_write.sum / nodes), scaled to the full launch by its node count;
-# profiles/k_viscous_fp64_jet256x128x64.md: (541.0 + 226.6) MB over 258 x 130 x 66 nodes.
-TRAFFIC_PER_NODE = {"viscous": 346.7}
+# profiles/k_viscous_fp64_jet256x128x64.md: (541.0 + 225.7) MB over 258 x 130 x 66 nodes.
+TRAFFIC_PER_NODE = {"viscous": 346.3}
 # k_fused32: (123 + 4 x 170) / 5 DRAM bytes per node over a step's five launches
 # (stage 1 and stage 2 captures of the current kernel in profiles/k_fused32_jet256x128x64.md).
 TRAFFIC_FUSED32_PER_NODE = (123.0 + 4 * 170.0) / 5
@@ -163,38 +163,43 @@ def run_reference(args):
 
 
 def run_paper_meshes(args, jz, W, torch):
-    """Single-GPU throughput on the paper's Table "mesh" shapes (nk = 360 unique azimuthal points)."""
-    free, total = torch.cuda.mem_get_info()
+    """Single-GPU throughput on the paper's Table "mesh" shapes (nk = 360 unique azimuthal points).
+
+    Per mesh: the FP64 form if its 600 bytes per padded node fit, then the FP32-flux form on the
+    full grid if that fits, else on a compact grid (FP32 metrics only, jz_grid_compact)."""
     rows = []
     for name in args.paper_meshes.split(","):
         ni, nj = W.PAPER_MESHES[name]
         nk = 360
         npts = ni * nj * nk
-        row = {"mesh": name, "shape": [ni, nj, nk], "points": npts}
-        xyz = W.jet_grid_device(ni, nj, nk)
-        q = W.jet_state_device(xyz)
-        prm = W.jet_params(seed=2)
         padded = ((ni + 4 + 3) // 4 * 4) * (nj + 4) * (nk + 4)
+        row = {"mesh": name, "shape": [ni, nj, nk], "points": npts, "fp64": None, "fp32flux": None}
+        prm = W.jet_params(seed=2)
         free, _ = torch.cuda.mem_get_info()
-        if 216 * padded > 0.9 * free:          # 18 grid fields + 9 metric scratch fields
-            row["fp32flux"] = row["fp64"] = None
-            rows.append(row)
+        if (24 * npts + 144 * padded) > 0.9 * free or 216 * padded > 0.9 * free:
+            rows.append(row)                         # grid construction itself does not fit
             print(json.dumps(row), flush=True)
             continue
-        grid = jz.Grid(ni, nj, nk, xyz, W.TOPO_JET)
-        grid._xyz = None
+        xyz = W.jet_grid_device(ni, nj, nk)
+        grid = jz.Grid(ni, nj, nk, xyz, W.TOPO_JET, metrics=False)
         del xyz
         torch.cuda.empty_cache()
-        # solver bytes per padded node: FP32-flux 3 x 5 FP64 state fields + 10 FP32 metrics;
-        # FP64 3 x 5 state fields + 42 stage-scratch fields
-        for form, prec, per_node in (("fp32flux", jz.JZ_PREC_FP32FLUX, 160), ("fp64", jz.JZ_PREC_FP64, 456)):
-            free, _ = torch.cuda.mem_get_info()
-            if per_node * padded > 0.9 * free:
-                row[form] = None
-                continue
+        grid.compute_metrics()
+
+        def state():
+            x = W.jet_grid_device(ni, nj, nk)
+            q = W.jet_state_device(x)
+            del x
+            torch.cuda.empty_cache()
+            return q
+
+        def timed(prec):
+            q = state()
             stream = torch.cuda.Stream()
             s = jz.Solver(grid, prm, prec, stream=stream.cuda_stream)
             s.set_state(q, 0.0)
+            del q
+            torch.cuda.empty_cache()
             for _ in range(max(args.warmup, 1)):
                 s.step(1, stats=False)
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -204,11 +209,25 @@ def run_paper_meshes(args, jz, W, torch):
             torch.cuda.synchronize()
             ms = e0.elapsed_time(e1) / args.steps
             st = s.step(0, stats=True)
-            row[form] = {"ms_per_step": ms, "gpoint_stage_per_s": npts * 5 / (ms / 1e3) / 1e9, "min_p": st.min_p}
             s.close()
             torch.cuda.empty_cache()
+            return {"ms_per_step": ms, "gpoint_stage_per_s": npts * 5 / (ms / 1e3) / 1e9, "min_p": st.min_p}
+
+        free, _ = torch.cuda.mem_get_info()
+        if 456 * padded + 40 * npts + 24 * npts < 0.9 * free:
+            row["fp64"] = timed(jz.JZ_PREC_FP64)
+            row["fp64"]["grid"] = "full"
+        free, _ = torch.cuda.mem_get_info()
+        mode = "full"
+        if 160 * padded + 40 * npts + 24 * npts > 0.9 * free:
+            grid.compact()                           # frees 104 B per padded node
+            torch.cuda.empty_cache()
+            mode = "compact"
+        free, _ = torch.cuda.mem_get_info()
+        if (160 if mode == "full" else 120) * padded + 64 * npts < 0.9 * free:
+            row["fp32flux"] = timed(jz.JZ_PREC_FP32FLUX)
+            row["fp32flux"]["grid"] = mode
         grid.close()
-        del q
         torch.cuda.empty_cache()
         rows.append(row)
         print(json.dumps(row), flush=True)

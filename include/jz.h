@@ -103,7 +103,9 @@ const char* jz_last_error(void);
 int jz_version(void);
 
 /* Create a grid from node coordinates (paper Algorithm 2: Read(Mesh)).
- *  xyz     [3][nk][nj][ni] Cartesian node coordinates, host or device.
+ *  xyz     [3][nk][nj][ni] Cartesian node coordinates, host or device
+ *          (device coordinates are padded directly, host ones through a
+ *          temporary device copy of the same size).
  *  period  [3][3] shift vectors of the i, j, k periods (JZ_TOPO_PERIODIC),
  *          host memory; may be NULL for JZ_TOPO_JET (ignored there).
  *  Sizes: JZ_TOPO_PERIODIC needs ni, nj, nk >= 1; JZ_TOPO_JET needs ni >= 4,
@@ -125,8 +127,24 @@ int jz_destroy_grid(jz_grid* g);
 int jz_compute_metrics(jz_grid* g);
 
 /* Copy the metrics to out [10][N] (host or device): S^xi_{x,y,z},
- * S^eta_{x,y,z}, S^zeta_{x,y,z}, V.  JZ_ERR_STATE before jz_compute_metrics. */
+ * S^eta_{x,y,z}, S^zeta_{x,y,z}, V.  JZ_ERR_STATE before jz_compute_metrics
+ * and on a compact grid. */
 int jz_get_metrics(const jz_grid* g, double* out);
+
+/* Compact a grid for the FP32-flux form (no counterpart in the paper; it
+ * lets one GPU hold the paper's largest mesh, 1700 x 1700 x 361 points).
+ * The metrics are converted to FP32 once and kept by the grid (S^xi, S^eta,
+ * S^zeta, V: 40 bytes per padded node), the far-field normals and the
+ * entrance-plane coordinates stay in FP64 surface arrays, and the FP64
+ * coordinates and metrics (144 bytes per padded node) are freed.
+ * Afterwards: FP32-flux solvers use the grid's FP32 metrics instead of their
+ * own copy; the CFL rate of the first step after jz_set_state and the
+ * conservation totals use the FP32 metrics widened to FP64 (relative
+ * differences ~1e-7 from a full grid); FP64 solvers, jz_get_metrics and
+ * jz_residual_noalloc refuse the grid (JZ_ERR_STATE).  Idempotent.
+ * Errors: JZ_ERR_STATE (metrics not computed; a solver still uses the grid),
+ * JZ_ERR_OOM, JZ_ERR_CUDA.  Synchronous (legacy default stream). */
+int jz_grid_compact(jz_grid* g);
 
 /* Create a solver on a grid with computed metrics (Algorithm 2: Read(Input)).
  *  stream  a cudaStream_t (may be NULL).  Allocates the state and the
@@ -244,6 +262,17 @@ int jz_stats_end(jz_solver* s);
  * drops.  Both return JZ_ERR_ARG on NULL pointers or ni < 2. */
 int jz_station_profile(const double* field, const double* x, int ni, int nj, double x0, double* out);
 int jz_potential_core(const double* axis, const double* x, int ni, double u_jet, double frac, double* x_core);
+
+/* ---- arithmetic self-check -------------------------------------------------- *
+ * The FP64 form computes reciprocals (1/rho, the Sutherland and pressure-sensor
+ * denominators) and the cube roots of the anisotropic spectral-radius scaling
+ * with the library's own routines: a hardware reciprocal seed refined by two
+ * Newton-Raphson steps, and an FP32 seed of x^(1/3) refined by one Halley step.
+ * jz_check_math runs both on 2^20 arguments spread over [1e-30, 1e30] on the
+ * current device and returns the largest relative error against IEEE division
+ * (1.0/x) and the CUDA math library's cbrt.  No counterpart in the paper.
+ * Synchronous (legacy default stream).  Errors: JZ_ERR_ARG (NULL), JZ_ERR_CUDA. */
+int jz_check_math(double* rcp_max_rel, double* cbrt_max_rel);
 
 /* ---- snapshots (checkpoint / restart) ------------------------------------ *
  * The paper restarts long runs from stored solution files (Algorithm 2

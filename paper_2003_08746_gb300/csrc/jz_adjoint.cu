@@ -495,7 +495,8 @@ __global__ void k_adj_farfield(Dims d, Consts c, GridDev g, State q, Adj64 a) {
   const int i = 1 + (int)(t % ni2), k = (int)(t / ni2);
   const int jb = d.nj - 1;
   const long long pb = pidx(d, i, jb, k), pi = pidx(d, i, jb - 1, k);
-  const double sx = g.S[3][pb], sy = g.S[4][pb], sz = g.S[5][pb];
+  const long long nsurf = (long long)d.nk * d.ni, isurf = (long long)k * d.ni + i;
+  const double sx = g.Sb[isurf], sy = g.Sb[nsurf + isurf], sz = g.Sb[2 * nsurf + isurf];
   const double nm = sqrt(sx * sx + sy * sy + sz * sz);
   const double n[3] = {sx / nm, sy / nm, sz / nm};
   double Qi[5];

@@ -79,7 +79,9 @@ struct jz_grid {
   jz::Dims d;
   jz::GridDev g;
   bool metrics = false;
-  DevMem mem;
+  int nsolvers = 0;               // live solvers on this grid
+  DevMem mem64;                   // FP64 coordinates and metrics (released by jz_grid_compact)
+  DevMem mem;                     // surface copies; FP32 metrics of a compact grid
 };
 
 struct jz_solver {
@@ -322,23 +324,34 @@ int jz_create_grid(int ni, int nj, int nk, const double* xyz, const double* peri
                       &g->g.S[3], &g->g.S[4], &g->g.S[5], &g->g.S[6], &g->g.S[7], &g->g.S[8],
                       &g->g.V, &g->g.invV, &g->g.Smag[0], &g->g.Smag[1], &g->g.Smag[2], &g->g.Delta};
   for (double** sl : slots) {
-    *sl = g->mem.alloc(d.Np, e, nullptr);
+    *sl = g->mem64.alloc(d.Np, e, nullptr);
     if (!*sl || e != cudaSuccess) {
       delete g;
       return fail(JZ_ERR_OOM, "grid arrays: %s", cudaGetErrorString(e));
     }
   }
-  const long long N = npts(d);
-  double* tmp = nullptr;
-  e = cudaMalloc(&tmp, 3 * sizeof(double) * N);
+  g->g.Sb = g->mem.alloc(3 * (size_t)d.nk * d.ni, e, nullptr);
+  if (e == cudaSuccess) g->g.Xin = g->mem.alloc(2 * (size_t)d.nk * d.nj, e, nullptr);
   if (e != cudaSuccess) {
     delete g;
-    return fail(JZ_ERR_OOM, "coordinate staging: %s", cudaGetErrorString(e));
+    return fail(JZ_ERR_OOM, "grid surface arrays: %s", cudaGetErrorString(e));
   }
-  e = cudaMemcpy(tmp, xyz, 3 * sizeof(double) * N, cudaMemcpyDefault);
-  if (e == cudaSuccess) e = jz::pad_coordinates(d, tmp, period, g->g, nullptr);
+  const long long N = npts(d);
+  // coordinates already on the device are padded in place; host ones go through a staging copy
+  const double* src = xyz;
+  double* tmp = nullptr;
+  if (!is_device_ptr(xyz)) {
+    e = cudaMalloc(&tmp, 3 * sizeof(double) * N);
+    if (e != cudaSuccess) {
+      delete g;
+      return fail(JZ_ERR_OOM, "coordinate staging: %s", cudaGetErrorString(e));
+    }
+    e = cudaMemcpy(tmp, xyz, 3 * sizeof(double) * N, cudaMemcpyHostToDevice);
+    src = tmp;
+  }
+  if (e == cudaSuccess) e = jz::pad_coordinates(d, src, period, g->g, nullptr);
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
-  cudaFree(tmp);
+  if (tmp) cudaFree(tmp);
   if (e != cudaSuccess) {
     delete g;
     return fail(JZ_ERR_CUDA, "jz_create_grid: %s", cudaGetErrorString(e));
@@ -372,13 +385,41 @@ int jz_compute_metrics(jz_grid* g) {
   int nbad = 0;
   JZ_CK(cudaMemcpy(&nbad, bad, sizeof(int), cudaMemcpyDeviceToHost));
   if (nbad) return fail(JZ_ERR_ARG, "grid has %d advanced nodes with V <= 0", nbad);
+  JZ_CK(jz::boundary_copies(d, g->g, nullptr));
+  JZ_CK(cudaDeviceSynchronize());
   g->metrics = true;
+  return JZ_OK;
+}
+
+int jz_grid_compact(jz_grid* g) {
+  if (!g) return fail(JZ_ERR_ARG, "jz_grid_compact: NULL grid");
+  if (!g->metrics) return fail(JZ_ERR_STATE, "jz_grid_compact: call jz_compute_metrics first");
+  if (g->g.compact) return JZ_OK;
+  if (g->nsolvers > 0) return fail(JZ_ERR_STATE, "jz_grid_compact: %d solver(s) still use the grid", g->nsolvers);
+  const jz::Dims& d = g->d;
+  cudaError_t e = cudaSuccess;
+  float* Sf[10];
+  for (int i = 0; i < 10 && e == cudaSuccess; ++i)
+    Sf[i] = reinterpret_cast<float*>(g->mem.alloc((d.Np + 1) / 2, e, nullptr));
+  float** table = nullptr;
+  if (e == cudaSuccess) table = reinterpret_cast<float**>(g->mem.alloc(10, e, nullptr));
+  if (e != cudaSuccess) return fail(JZ_ERR_OOM, "jz_grid_compact: %s", cudaGetErrorString(e));
+  JZ_CK(cudaMemcpy(table, Sf, sizeof Sf, cudaMemcpyHostToDevice));
+  JZ_CK(jz::metrics_to_f32(d, g->g, table, nullptr));
+  JZ_CK(cudaDeviceSynchronize());
+  g->mem64.release();
+  for (int c = 0; c < 3; ++c) g->g.xyz[c] = g->g.Smag[c] = nullptr;
+  for (int c = 0; c < 9; ++c) g->g.S[c] = nullptr;
+  g->g.V = g->g.invV = g->g.Delta = nullptr;
+  for (int i = 0; i < 10; ++i) g->g.Sf[i] = Sf[i];
+  g->g.compact = 1;
   return JZ_OK;
 }
 
 int jz_get_metrics(const jz_grid* g, double* out) {
   if (!g || !out) return fail(JZ_ERR_ARG, "jz_get_metrics: NULL argument");
   if (!g->metrics) return fail(JZ_ERR_STATE, "jz_get_metrics: metrics not computed");
+  if (g->g.compact) return fail(JZ_ERR_STATE, "jz_get_metrics: the grid is compact (FP32 metrics only)");
   const jz::Dims& d = g->d;
   double* M[10];
   for (int i = 0; i < 9; ++i) M[i] = g->g.S[i];
@@ -410,6 +451,8 @@ int jz_create(jz_grid* g, const jz_params* p, void* stream, jz_solver** out) {
     return fail(JZ_ERR_ARG, "jz_create: parameter out of range");
   if (p->precision != JZ_PREC_FP64 && p->precision != JZ_PREC_FP32FLUX)
     return fail(JZ_ERR_ARG, "jz_create: unknown precision %d", p->precision);
+  if (g->g.compact && p->precision != JZ_PREC_FP32FLUX)
+    return fail(JZ_ERR_STATE, "jz_create: a compact grid (FP32 metrics only) takes the FP32-flux form only");
   jz_solver* s = new (std::nothrow) jz_solver;
   if (!s) return fail(JZ_ERR_OOM, "host allocation failed");
   s->grid = g;
@@ -430,14 +473,18 @@ int jz_create(jz_grid* g, const jz_params* p, void* stream, jz_solver** out) {
   s->fp32 = p->precision == JZ_PREC_FP32FLUX;
   float** Sf_dev = nullptr;
   if (s->fp32) {
-    for (int i = 0; i < 10; ++i) {
+    if (g->g.compact) {
+      for (int i = 0; i < 10; ++i) s->Sf[i] = const_cast<float*>(g->g.Sf[i]);   // the grid's own
+    } else {
+      for (int i = 0; i < 10; ++i) {
+        double* tmp = nullptr;
+        A(tmp, (d.Np + 1) / 2);            // Np floats
+        s->Sf[i] = reinterpret_cast<float*>(tmp);
+      }
       double* tmp = nullptr;
-      A(tmp, (d.Np + 1) / 2);            // Np floats
-      s->Sf[i] = reinterpret_cast<float*>(tmp);
+      A(tmp, 10);
+      Sf_dev = reinterpret_cast<float**>(tmp);
     }
-    double* tmp = nullptr;
-    A(tmp, 10);
-    Sf_dev = reinterpret_cast<float**>(tmp);
     // CTAs of 30 x 8 columns; split k so that the grid covers the SMs evenly
     const int tx = jz::fused32_tile_x(), ty = jz::fused32_tile_y();
     const long long tiles = (long long)((d.ni + tx - 1) / tx) * ((d.nj + ty - 1) / ty);
@@ -467,7 +514,7 @@ int jz_create(jz_grid* g, const jz_params* p, void* stream, jz_solver** out) {
     delete s;
     return fail(JZ_ERR_OOM, "jz_create: device allocation failed: %s", cudaGetErrorString(e));
   }
-  if (s->fp32) {
+  if (s->fp32 && Sf_dev) {
     e = cudaMemcpyAsync(Sf_dev, s->Sf, sizeof(s->Sf), cudaMemcpyHostToDevice, s->st);
     if (e == cudaSuccess) e = jz::metrics_to_f32(d, g->g, Sf_dev, s->st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s->st);
@@ -485,6 +532,7 @@ int jz_create(jz_grid* g, const jz_params* p, void* stream, jz_solver** out) {
     }
   }
   s->n_adv = d.topo == JZ_TOPO_JET ? (long long)(d.ni - 2) * (d.nj - 2) * d.nk : npts(d);
+  g->nsolvers += 1;
   *out = s;
   return JZ_OK;
 }
@@ -492,6 +540,7 @@ int jz_create(jz_grid* g, const jz_params* p, void* stream, jz_solver** out) {
 int jz_destroy(jz_solver* s) {
   if (!s) return fail(JZ_ERR_ARG, "jz_destroy: NULL");
   cudaStreamSynchronize(s->st);
+  s->grid->nsolvers -= 1;
   delete s;
   return JZ_OK;
 }
@@ -968,6 +1017,20 @@ int jz_stats_end(jz_solver* s) {
   if (!s) return fail(JZ_ERR_ARG, "jz_stats_end: NULL solver");
   JZ_CK(cudaStreamSynchronize(s->st));
   s->free_stats();
+  return JZ_OK;
+}
+
+int jz_check_math(double* rcp_max_rel, double* cbrt_max_rel) {
+  if (!rcp_max_rel || !cbrt_max_rel) return fail(JZ_ERR_ARG, "jz_check_math: NULL argument");
+  double* dev = nullptr;
+  JZ_CK(cudaMalloc(&dev, 2 * sizeof(double)));
+  double h[2] = {0.0, 0.0};
+  cudaError_t e = jz::math_check(dev, nullptr);
+  if (e == cudaSuccess) e = cudaMemcpy(h, dev, sizeof h, cudaMemcpyDeviceToHost);
+  cudaFree(dev);
+  if (e != cudaSuccess) return fail(JZ_ERR_CUDA, "jz_check_math: %s", cudaGetErrorString(e));
+  *rcp_max_rel = h[0];
+  *cbrt_max_rel = h[1];
   return JZ_OK;
 }
 

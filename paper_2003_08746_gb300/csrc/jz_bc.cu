@@ -28,7 +28,8 @@ __global__ void k_farfield(Dims d, Consts c, GridDev g, State q) {
   const int i = 1 + (int)(t % ni2), k = (int)(t / ni2);
   const int jb = d.nj - 1;
   const long long pb = pidx(d, i, jb, k), pi = pidx(d, i, jb - 1, k);
-  const double sx = g.S[3][pb], sy = g.S[4][pb], sz = g.S[5][pb];
+  const long long nb = (long long)d.nk * d.ni, sb = (long long)k * d.ni + i;
+  const double sx = g.Sb[sb], sy = g.Sb[nb + sb], sz = g.Sb[2 * nb + sb];
   const double nm = sqrt(sx * sx + sy * sy + sz * sz);
   const double n[3] = {sx / nm, sy / nm, sz / nm};
   const double rho_i = q.q[0][pi];
@@ -134,8 +135,7 @@ __global__ void k_build_inflow(Dims d, Consts c, GridDev g, double* u0, double* 
   const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (t >= (long long)d.nj * d.nk) return;
   const int j = (int)(t % d.nj), k = (int)(t / d.nj);
-  const long long p = pidx(d, 0, j, k);
-  const double y = g.xyz[1][p], z = g.xyz[2][p];
+  const double y = g.Xin[t], z = g.Xin[(long long)d.nj * d.nk + t];   // t = k nj + j
   const double r = sqrt(y * y + z * z);
   const double th = atan2(z, y);
   u0[t] = 0.5 * c.jet_mach * (1.0 + tanh((0.5 - r) / (2.0 * c.theta_mom)));

@@ -258,6 +258,31 @@ cudaError_t ghost_fill(const Dims& d, double* const* f, int nvar, cudaStream_t s
   return cudaGetLastError();
 }
 
+// Surface copies: the far-field normals S^eta at j = nj-1 ([3][nk][ni]) and the
+// entrance-plane coordinates y, z at i = 0 ([2][nk][nj]).
+__global__ void k_boundary_copies(Dims d, GridDev g) {
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long nb = (long long)d.nk * d.ni, ne = (long long)d.nk * d.nj;
+  if (t < 3 * nb) {
+    const int c = (int)(t / nb);
+    const long long r = t % nb;
+    const int k = (int)(r / d.ni), i = (int)(r % d.ni);
+    g.Sb[t] = g.S[3 + c][pidx(d, i, d.nj - 1, k)];
+  } else if (t < 3 * nb + 2 * ne) {
+    const long long u = t - 3 * nb;
+    const int c = (int)(u / ne);
+    const long long r = u % ne;
+    const int k = (int)(r / d.nj), j = (int)(r % d.nj);
+    g.Xin[u] = g.xyz[1 + c][pidx(d, 0, j, k)];
+  }
+}
+
+cudaError_t boundary_copies(const Dims& d, const GridDev& g, cudaStream_t st) {
+  const long long n = 3LL * d.nk * d.ni + 2LL * d.nk * d.nj;
+  k_boundary_copies<<<blocks_for(n, kTPB), kTPB, 0, st>>>(d, g);
+  return cudaGetLastError();
+}
+
 cudaError_t metrics_to_f32(const Dims& d, const GridDev& g, float* const* dst_dev, cudaStream_t st) {
   double* M[10];
   for (int i = 0; i < 9; ++i) M[i] = g.S[i];

@@ -41,6 +41,44 @@ inline Dims make_dims(int ni, int nj, int nk, int topo) {
   return d;
 }
 
+// FP64 reciprocal and cube root with fewer FP64-pipe instructions than IEEE
+// division and the library cube root; the FP64 form is bound by that pipe.
+// Both are accurate to about one unit in the last place (checked against
+// 1.0/x and cbrt(x) by jz_check_math), far inside the form's 1e-12 parity.
+//
+// rcp64: for normal, finite x != 0.  Seed: the hardware approximation
+// rcp.approx.ftz.f64 (about 2^-22 relative); two Newton-Raphson steps
+// r <- r + r (1 - x r) square the error each time (2^-44, then rounding).
+__device__ __forceinline__ double rcp64(double x) {
+  double r;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(x));
+  double e = fma(-x, r, 1.0);
+  r = fma(r, e, r);
+  e = fma(-x, r, 1.0);
+  return fma(r, e, r);
+}
+
+// cbrt64: x^(1/3) for x >= 0.  For 2^-100 <= x < 2^101 the seed is
+// 2^(log2(x)/3) in FP32 (MUFU, about 1e-7 relative), with the FP64 <-> FP32
+// conversions done by integer operations on the IEEE fields (mantissa
+// truncated; exponent re-biased by 1023 - 127 = 896) so that they stay off
+// the FP64 pipe; then one step of Halley's method for y^3 = x,
+//   y <- y (y^3 + 2x) / (2 y^3 + x),
+// whose error shrinks cubically (1e-7 -> below rounding), with the quotient
+// formed by rcp64.  Other x (0, tiny, huge) use the library cube root.
+__device__ __forceinline__ double cbrt64(double x) {
+  const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+  if (hi - ((1023u - 100u) << 20) >= (201u << 20)) return cbrt(x);
+  const float xf = __uint_as_float(((hi - (896u << 20)) << 3) | (lo >> 29));
+  float l, yf;
+  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(l) : "f"(xf));
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(yf) : "f"(l * (1.0f / 3.0f)));
+  const unsigned yb = __float_as_uint(yf);
+  const double y = __hiloint2double((int)((yb >> 3) + (896u << 20)), (int)(yb << 29));
+  const double y3 = y * y * y;
+  return y * fma(2.0, x, y3) * rcp64(fma(2.0, y3, x));
+}
+
 // Grid arrays on the device (padded, ghost-filled).
 struct GridDev {
   double* xyz[3];
@@ -49,6 +87,13 @@ struct GridDev {
   double* invV;       // 1/V (0 where V = 0, i.e. on the jet axis)
   double* Smag[3];    // |S^dir|
   double* Delta;      // filter width V^(1/3)
+  // surface copies kept by every grid (also compact ones)
+  double* Sb;         // far-field normals S^eta at j = nj-1: [3][nk][ni]
+  double* Xin;        // entrance-plane coordinates y, z at i = 0: [2][nk][nj]
+  // compact grids (jz_grid_compact): the FP64 arrays above except Sb and Xin are
+  // released and the metrics are kept in FP32 only
+  int compact;
+  const float* Sf[10];  // S^xi, S^eta, S^zeta (9), V in FP32 (compact grids)
 };
 
 // Derived constants of the non-dimensional formulation, by value.
@@ -151,6 +196,7 @@ cudaError_t compute_metrics(const Dims& d, GridDev& g, double* scratch9[9], cuda
 // ghost fill of nvar padded fields by the state's ghost map
 cudaError_t ghost_fill(const Dims& d, double* const* f, int nvar, cudaStream_t st);
 // FP32 copy of the metrics S (9) and V; dst_dev is a device array of 10 pointers
+cudaError_t boundary_copies(const Dims& d, const GridDev& g, cudaStream_t st);
 cudaError_t metrics_to_f32(const Dims& d, const GridDev& g, float* const* dst_dev, cudaStream_t st);
 // copy between unpadded [nvar][N] and padded real region
 cudaError_t pack_real(const Dims& d, double* const* padded, const double* flat, int nvar,
@@ -188,6 +234,8 @@ int stat_partial_count();
 cudaError_t stats_with(const Dims& d, const Consts& c, const GridDev& g, const State& q, Scalars* sc,
                        double* part, cudaStream_t st);
 cudaError_t check_volume(const Dims& d, const GridDev& g, int* bad, cudaStream_t st);
+// self-check of rcp64 / cbrt64 (jz_mathcheck.cu)
+cudaError_t math_check(double* dev_maxrel2, cudaStream_t st);
 // flow statistics of the axial velocity (jz_stats.cu)
 cudaError_t flow_sample(const Dims& d, const State& q, double* mean, double* m2, long long n, cudaStream_t st);
 cudaError_t flow_final(const Dims& d, const double* mean, const double* m2, long long n, double* out_mean,

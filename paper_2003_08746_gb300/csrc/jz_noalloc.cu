@@ -68,6 +68,7 @@ extern "C" int jz_residual_noalloc(const jz_grid* g, const jz_params* p, const d
   Dims d;
   GridDev gd;
   if (!grid_view(g, &d, &gd)) return set_error(JZ_ERR_STATE, "jz_residual_noalloc: metrics not computed");
+  if (gd.compact) return set_error(JZ_ERR_STATE, "jz_residual_noalloc: the grid is compact (FP32 metrics only)");
   if (p->precision != JZ_PREC_FP64)
     return set_error(JZ_ERR_ARG, "jz_residual_noalloc: only the FP64 form is available");
   if (!(p->gamma > 1.0) || !(p->Re > 0.0) || !(p->Pr > 0.0) || !(p->Pr_sgs > 0.0) || !(p->T_ref_K > 0.0) ||

@@ -26,12 +26,23 @@ __global__ void k_cfl_rate(Dims d, GridDev g, State q, Consts c, Scalars* sc) {
     const double pr = c.gm1 * (q.q[4][p] - 0.5 * (m1 * u + m2 * v + m3 * w));
     const double a = sqrt(c.gamma * pr / rho);
     double lsum = 0.0;
-    for (int dir = 0; dir < 3; ++dir) {
-      const double U = g.S[3 * dir][p] * u + g.S[3 * dir + 1][p] * v + g.S[3 * dir + 2][p] * w;
-      const double lam = fabs(U) + a * g.Smag[dir][p];
-      lsum = dir == 0 ? lam : lsum + lam;
+    if (!g.compact) {
+      for (int dir = 0; dir < 3; ++dir) {
+        const double U = g.S[3 * dir][p] * u + g.S[3 * dir + 1][p] * v + g.S[3 * dir + 2][p] * w;
+        const double lam = fabs(U) + a * g.Smag[dir][p];
+        lsum = dir == 0 ? lam : lsum + lam;
+      }
+      rate = lsum * g.invV[p];
+    } else {
+      // compact grid: the same rate from the FP32 metrics, widened
+      for (int dir = 0; dir < 3; ++dir) {
+        const double sx = g.Sf[3 * dir][p], sy = g.Sf[3 * dir + 1][p], sz = g.Sf[3 * dir + 2][p];
+        const double lam = fabs(sx * u + sy * v + sz * w) + a * sqrt(sx * sx + sy * sy + sz * sz);
+        lsum = dir == 0 ? lam : lsum + lam;
+      }
+      const double V = g.Sf[9][p];
+      rate = V > 0.0 ? lsum / V : 0.0;
     }
-    rate = lsum * g.invV[p];
   }
   __shared__ double red[kTPB / 32];
   rate = warp_max(rate);
@@ -69,7 +80,7 @@ __global__ void k_stats_partial(Dims d, GridDev g, State q, Consts c, double* pa
     const long long r = t / d.ni;
     const int j = (int)(r % d.nj), k = (int)(r / d.nj);
     const long long p = pidx(d, i, j, k);
-    const double V = g.V[p];
+    const double V = g.compact ? (double)g.Sf[9][p] : g.V[p];
     double qq[5];
     for (int m = 0; m < 5; ++m) {
       qq[m] = q.q[m][p];

@@ -33,7 +33,7 @@ __device__ __forceinline__ void aniso(const Consts& c, const double lam[3], doub
   double lo[3], hi[3];
   if (c.sigma_is_two_thirds) {
     for (int d = 0; d < 3; ++d) {
-      const double t = cbrt(lam[d]);
+      const double t = cbrt64(lam[d]);
       lo[d] = t;
       hi[d] = t * t;
     }
@@ -54,13 +54,13 @@ __global__ void __launch_bounds__(kTPB) k_nodal(Dims d, Consts c, GridDev g, Wor
   if (!box_coord(b, blockIdx.x * (long long)blockDim.x + threadIdx.x, i, j, k)) return;
   const long long p = pidx(d, i, j, k);
   const double rho = q.q[0][p], m1 = q.q[1][p], m2 = q.q[2][p], m3 = q.q[3][p], e = q.q[4][p];
-  const double ir = 1.0 / rho;                  // one reciprocal instead of four divisions
+  const double ir = rcp64(rho);                 // one reciprocal instead of four divisions
   const double u = m1 * ir, v = m2 * ir, ww = m3 * ir;
   const double pr = c.gm1 * (e - 0.5 * (m1 * u + m2 * v + m3 * ww));
   const double T = c.gamma * pr * ir;
   const double a = sqrt(T);
   // Sutherland, eq. (sutherland), with T_inf = 1
-  const double mu = c.mu_ref * (T * a) * c.sut_num / (T + c.S_hat);
+  const double mu = c.mu_ref * (T * a) * c.sut_num * rcp64(T + c.S_hat);
   w.u[p] = u; w.v[p] = v; w.w[p] = ww; w.T[p] = T; w.p[p] = pr; w.mu[p] = mu;
   double lam[3];
   for (int dir = 0; dir < 3; ++dir) {
@@ -124,16 +124,16 @@ __global__ void __launch_bounds__(kTPB) k_viscous(Dims d, Consts c, GridDev g, W
     F[jj][2] = tau[2][jj];
     F[jj][3] = vel[0] * tau[0][jj] + vel[1] * tau[1][jj] + vel[2] * tau[2][jj] + k_eff * L[3][jj];
   }
+  // H^dir -= S^dir_j F_j, as three fused multiply-adds onto the stored E^dir
   for (int dir = 0; dir < 3; ++dir)
-    for (int m = 0; m < 4; ++m) {
-      const double fv = S[dir][0] * F[0][m] + S[dir][1] * F[1][m] + S[dir][2] * F[2][m];
-      w.H[dir][m + 1][p] = w.H[dir][m + 1][p] - fv;
-    }
-  // pressure sensor along each direction
+    for (int m = 0; m < 4; ++m)
+      w.H[dir][m + 1][p] = fma(-S[dir][2], F[2][m], fma(-S[dir][1], F[1][m], fma(-S[dir][0], F[0][m],
+                                                                                 w.H[dir][m + 1][p])));
+  // pressure sensor along each direction: |p+ - 2p + p-| / (p+ + 2p + p-)
   const double pc = w.p[p];
   for (int dir = 0; dir < 3; ++dir) {
-    const double pp = w.p[p + s[dir]], pm = w.p[p - s[dir]];
-    w.nu[dir][p] = fabs(pp - 2.0 * pc + pm) / (pp + 2.0 * pc + pm);
+    const double sum = w.p[p + s[dir]] + w.p[p - s[dir]];
+    w.nu[dir][p] = fabs(fma(-2.0, pc, sum)) * rcp64(fma(2.0, pc, sum));
   }
 }
 
@@ -150,12 +150,15 @@ __global__ void __launch_bounds__(kTPB) k_faces(Dims d, Consts c, Work64 w, Stat
     const double k4 = c.kappa4 - eps2;
     const double eps4 = k4 > 0.0 ? k4 : 0.0;
     const double Lf = 0.5 * (w.Lam[dir][p] + w.Lam[dir][p + sd]);
+    // Lf (eps2 d1 - eps4 d3) with d3 = (q2 - qm) - 3 d1, regrouped as
+    // (Lf eps2 + 3 Lf eps4) d1 - Lf eps4 (q2 - qm): two products per face and variable
+    const double b = Lf * eps4;
+    const double a3 = fma(3.0, b, Lf * eps2);
     for (int m = 0; m < 5; ++m) {
       const double* Q = q.q[m];
-      const double q0 = Q[p], q1 = Q[p + sd], q2 = Q[p + 2 * sd], qm = Q[p - sd];
-      const double d1 = q1 - q0;
-      const double d3 = q2 - 3.0 * q1 + 3.0 * q0 - qm;
-      w.D[dir][m][p] = Lf * (eps2 * d1 - eps4 * d3);
+      const double d1 = Q[p + sd] - Q[p];
+      const double e3 = Q[p + 2 * sd] - Q[p - sd];
+      w.D[dir][m][p] = fma(a3, d1, -(b * e3));
     }
   }
 }
@@ -173,17 +176,22 @@ __global__ void __launch_bounds__(kTPB) k_update(Dims d, GridDev g, Work64 w, St
     const long long p = pidx(d, i, j, k);
     const long long s[3] = {1, d.sj, d.sk};
     const bool adv = advanced(d, i, j);
-    const double iV = g.invV[p];
+    const double hV = 0.5 * g.invV[p];
     double R[5];
     for (int m = 0; m < 5; ++m) {
-      double dH = 0.0, dD = 0.0;
-      for (int dir = 0; dir < 3; ++dir) {
-        const double* H = w.H[dir][m];
-        const double* D = w.D[dir][m];
-        dH += H[p + s[dir]] - H[p - s[dir]];
-        dD += D[p] - D[p - s[dir]];
-      }
-      R[m] = (0.5 * dH - dD) * iV;
+      // V RHS = (1/2) sum_dir (H+ - H-) - sum_dir (D0 - D-), summed as
+      // (sum H+ - sum H-) - 2 (sum D0 - sum D-), then times 1/(2V)
+      const double* H0 = w.H[0][m];
+      const double* H1 = w.H[1][m];
+      const double* H2 = w.H[2][m];
+      const double* D0 = w.D[0][m];
+      const double* D1 = w.D[1][m];
+      const double* D2 = w.D[2][m];
+      const double hp = (H0[p + s[0]] + H1[p + s[1]]) + H2[p + s[2]];
+      const double hm = (H0[p - s[0]] + H1[p - s[1]]) + H2[p - s[2]];
+      const double dp = (D0[p] + D1[p]) + D2[p];
+      const double dm = (D0[p - s[0]] + D1[p - s[1]]) + D2[p - s[2]];
+      R[m] = fma(-2.0, dp - dm, hp - hm) * hV;
     }
     if (MODE == 0) {
       const double adt = alpha * sc->dt;

@@ -28,7 +28,8 @@ EXPORTS = ("jz_last_error", "jz_version", "jz_create_grid", "jz_destroy_grid", "
            "jz_get_metrics", "jz_create", "jz_destroy", "jz_set_state", "jz_get_state", "jz_residual",
            "jz_rk_step", "jz_profile", "jz_profile_read", "jz_profile_name", "jz_residual_noalloc",
            "jz_adjoint_step", "jz_save_snapshot", "jz_load_snapshot", "jz_stats_begin", "jz_stats_sample",
-           "jz_stats_read", "jz_stats_end", "jz_station_profile", "jz_potential_core")
+           "jz_stats_read", "jz_stats_end", "jz_station_profile", "jz_potential_core", "jz_check_math",
+           "jz_grid_compact")
 JZ_NOALLOC_SCRATCH_BYTES = 64 * 1024 * 1024
 JZ_NPROF = 10
 
@@ -89,6 +90,8 @@ def load(path: str | None = None) -> ctypes.CDLL:
         "jz_adjoint_step": ([vp, vp, i, i, d, ctypes.POINTER(ctypes.c_double), vp], i),
         "jz_save_snapshot": ([vp, ctypes.c_char_p], i),
         "jz_load_snapshot": ([vp, ctypes.c_char_p], i),
+        "jz_grid_compact": ([vp], i),
+        "jz_check_math": ([ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)], i),
         "jz_stats_begin": ([vp, i], i),
         "jz_stats_sample": ([vp], i),
         "jz_stats_read": ([vp, vp, vp, ctypes.POINTER(ctypes.c_longlong)], i),
@@ -189,6 +192,17 @@ def jz_residual_noalloc(grid_h, params: jz_params, q, rhs, stream=None):
     """Residual with the library's fixed scratch array (no device allocation); device q and rhs."""
     st = ctypes.c_void_p(0 if stream is None else int(stream))
     _check(load().jz_residual_noalloc(grid_h, ctypes.byref(params), _ptr(q), _ptr(rhs), st))
+
+
+def jz_grid_compact(grid_h) -> None:
+    _check(load().jz_grid_compact(grid_h))
+
+
+def jz_check_math():
+    """(max relative error of the library's FP64 reciprocal, of its cube root) on the device."""
+    a, b = ctypes.c_double(), ctypes.c_double()
+    _check(load().jz_check_math(ctypes.byref(a), ctypes.byref(b)))
+    return a.value, b.value
 
 
 def jz_stats_begin(h, every: int) -> None:
@@ -327,11 +341,19 @@ def jz_profile_read(h):
 class Grid:
     """Owner of a jz_grid handle; metrics are computed on construction."""
 
-    def __init__(self, ni, nj, nk, xyz, topology, period=None):
+    def __init__(self, ni, nj, nk, xyz, topology, period=None, metrics=True):
+        """metrics=False leaves jz_compute_metrics to the caller (e.g. after freeing xyz)."""
         self.ni, self.nj, self.nk, self.topology = int(ni), int(nj), int(nk), int(topology)
-        self._xyz = xyz
         self.h = jz_create_grid(self.ni, self.nj, self.nk, xyz, period, self.topology)
+        if metrics:
+            jz_compute_metrics(self.h)
+
+    def compute_metrics(self):
         jz_compute_metrics(self.h)
+
+    def compact(self):
+        """Keep FP32 metrics only (FP32-flux solvers; frees 104 bytes per padded node)."""
+        jz_grid_compact(self.h)
 
     @classmethod
     def from_workload(cls, g):

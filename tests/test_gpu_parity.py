@@ -210,3 +210,13 @@ def test_jet_subsample_500_steps_fp64(jz):
     e2, em = field_errors(got, ref.numpy())
     print(f"jet64x32x16 FP64 500 steps vs oracle: rel L2 {e2}, rel max {em}")
     assert e2.max() <= TOL_L2, e2
+
+
+def test_fp64_reciprocal_and_cube_root(jz):
+    """The FP64 form's own reciprocal (Newton-Raphson from the hardware seed) and cube root
+    (Halley from an FP32 seed) against IEEE division and the CUDA cbrt on 2^20 arguments over
+    [1e-30, 1e30]: within 2 and 4 units of 2^-52 relative."""
+    e_rcp, e_cbrt = jz.jz_check_math()
+    print(f"rcp64 max rel err {e_rcp:.3e}, cbrt64 max rel err {e_cbrt:.3e}")
+    assert e_rcp <= 2 * 2.0 ** -52
+    assert e_cbrt <= 4 * 2.0 ** -52
