@@ -76,8 +76,8 @@ struct DevMem {
 }  // namespace
 
 struct jz_grid {
-  jz::Dims d;
-  jz::GridDev g;
+  jz::Dims d{};
+  jz::GridDev g{};                // value-initialised: null pointers, compact = 0
   bool metrics = false;
   int nsolvers = 0;               // live solvers on this grid
   DevMem mem64;                   // FP64 coordinates and metrics (released by jz_grid_compact)
@@ -89,14 +89,14 @@ struct jz_solver {
   jz_params prm;
   jz::Consts c;
   cudaStream_t st = nullptr;
-  jz::State qn, qa, qb;
-  jz::Work64 w;
+  jz::State qn{}, qa{}, qb{};
+  jz::Work64 w{};
   bool fp32 = false;              // JZ_PREC_FP32FLUX form
   float* Sf[10] = {nullptr};      // FP32 metrics (FP32-flux form)
   int kchunk = 0;                 // k planes per CTA of the fused kernel
   bool rate_ready = false;        // a CFL rate of Q^n is in Scalars::rate_max
   jz::Scalars* sc = nullptr;
-  jz::Inflow in;
+  jz::Inflow in{};
   double* part = nullptr;
   double* staging = nullptr;      // [5][N], allocated on first host transfer
   // flow statistics (jz_stats_*): per-node mean and M2, outputs [2][nj][ni]
