@@ -162,6 +162,68 @@ def run_reference(args):
     return 0
 
 
+def run_configs_table(args, jz, W, torch):
+    """Per workload of the build's config list: GPU FP64 and FP32-flux rates (CUDA events on the
+    solver stream, 2 warm-up steps) and the oracle's rate on the host with one thread and with
+    all threads (2 RK steps; the 1000 x 400 x 500 and 512 x 256 x 128 workloads are timed on the
+    oracle through bounded samples of the same recipe)."""
+    from oracle import jz_oracle as O
+    hbm = 6766.0
+    if os.path.exists(PEAKS_FILE):
+        hbm = float(json.load(open(PEAKS_FILE)).get("hbm_gbs", hbm))
+    cases = [("box32x24x16", 10, "box32x24x16"), ("jet256x128x64", 100, "jet256x128x64"),
+             ("jet512x256x128", 20, "jet64x32x16"), ("jet128x96x64", 20, "jet128x96x64"),
+             ("jet1000x400x500", 5, None)]
+    all_threads = torch.get_num_threads()
+    rows = []
+    for name, steps, oracle_case in cases:
+        g, q, prm = W.make_workload(name)
+        grid = jz.Grid.from_workload(g)
+        qd = torch.from_numpy(q).cuda()
+        del q
+        row = {"workload": name, "points": g.npts, "gpu_steps": steps}
+        for form, prec in (("fp64", jz.JZ_PREC_FP64), ("fp32flux", jz.JZ_PREC_FP32FLUX)):
+            stream = torch.cuda.Stream()
+            s = jz.Solver(grid, prm, prec, stream=stream.cuda_stream)
+            s.set_state(qd, 0.0)
+            s.step(2, stats=False)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            s.step(steps, stats=False)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / steps
+            rate = g.npts * 5 / (ms / 1e3)
+            bytes_ps = 192 if form == "fp64" else 152
+            row[form] = {"ms_per_step": ms, "gpoint_stage_per_s": rate / 1e9,
+                         "hbm_frac_algorithmic": rate * bytes_ps / 1e9 / hbm}
+            s.close()
+        grid.close()
+        del qd
+        torch.cuda.empty_cache()
+        # oracle on the host: the workload itself where it is small, else a bounded sample
+        if oracle_case is None:
+            og_shape = (200, 80, 100)
+            og = W.jet_grid(*og_shape, axial_stretch=True)
+            oq, oprm = W.jet_state(og), W.jet_params(seed=2)
+            label = "jet 200x80x100 sample"
+        else:
+            og, oq, oprm = W.make_workload(oracle_case)
+            label = oracle_case
+        ogrid, oc = O.Grid(og.ni, og.nj, og.nk, og.xyz, og.topology, og.period), O.Consts(oprm)
+        for key, nth in (("oracle_1thread", 1), ("oracle_all", all_threads)):
+            torch.set_num_threads(nth)
+            t0 = time.perf_counter()
+            O.run(ogrid, torch.from_numpy(oq), oc, 2)
+            dt = time.perf_counter() - t0
+            row[key] = {"gpoint_stage_per_s": og.npts * 10 / dt / 1e9, "threads": nth, "on": label, "seconds": dt}
+        torch.set_num_threads(all_threads)
+        rows.append(row)
+        print(json.dumps(row), flush=True)
+    print(json.dumps({"configs_table": rows}), flush=True)
+    return 0
+
+
 def run_paper_meshes(args, jz, W, torch):
     """Single-GPU throughput on the paper's Table "mesh" shapes (nk = 360 unique azimuthal points).
 
@@ -247,6 +309,8 @@ def main():
     ap.add_argument("--no-fp32", action="store_true", help="skip the FP32-flux variant")
     ap.add_argument("--fp32-only", action="store_true", help="time only the FP32-flux form (profiling runs)")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint variant")
+    ap.add_argument("--configs-table", action="store_true", help="GPU FP64 / FP32-flux and oracle 1-thread / "
+                    "all-thread rates for every workload of the config list (one JSON line each)")
     ap.add_argument("--paper-meshes", default="", help="comma list of the paper's meshes (A..I) to time "
                     "on one GPU instead of the default run, e.g. A,B,C,D,E,F,G")
     args = ap.parse_args()
@@ -269,6 +333,8 @@ def main():
     jz.load()
     if args.paper_meshes:
         return run_paper_meshes(args, jz, W, torch)
+    if args.configs_table:
+        return run_configs_table(args, jz, W, torch)
 
     g, q, prm = W.make_workload(args.workload)
     npts = g.npts
