@@ -22,9 +22,10 @@ __global__ void k_cfl_rate(Dims d, GridDev g, State q, Consts c, Scalars* sc) {
       (d.topo != JZ_TOPO_JET || (i >= 1 && i <= d.ni - 2 && j >= 1 && j <= d.nj - 2))) {
     const long long p = pidx(d, i, j, k);
     const double rho = q.q[0][p], m1 = q.q[1][p], m2 = q.q[2][p], m3 = q.q[3][p];
-    const double u = m1 / rho, v = m2 / rho, w = m3 / rho;
+    const double ir = rcp64(rho);
+    const double u = m1 * ir, v = m2 * ir, w = m3 * ir;
     const double pr = c.gm1 * (q.q[4][p] - 0.5 * (m1 * u + m2 * v + m3 * w));
-    const double a = sqrt(c.gamma * pr / rho);
+    const double a = sqrt(c.gamma * pr * ir);
     double lsum = 0.0;
     if (!g.compact) {
       for (int dir = 0; dir < 3; ++dir) {

@@ -133,12 +133,11 @@ __device__ __forceinline__ void face_flux(const ConstsF& c, float La, float Lb, 
   const float eps2 = c.kappa2 * fmaxf(na, nb);
   const float eps4 = fmaxf(0.f, c.kappa4 - eps2);
   const float Lf = 0.5f * (La + Lb);
+  // Lf (eps2 d1 - eps4 d3) with d3 = (q2 - qm) - 3 d1, as (Lf eps2 + 3 Lf eps4) d1 - Lf eps4 (q2 - qm)
+  const float b = Lf * eps4;
+  const float a3 = fmaf(3.f, b, Lf * eps2);
 #pragma unroll
-  for (int m = 0; m < 5; ++m) {
-    const float d1 = q1[m] - q0[m];
-    const float d3 = (q2[m] - qm[m]) + 3.f * (q0[m] - q1[m]);
-    out[m] = Lf * (eps2 * d1 - eps4 * d3);
-  }
+  for (int m = 0; m < 5; ++m) out[m] = fmaf(a3, q1[m] - q0[m], -b * (q2[m] - qm[m]));
 }
 
 struct Args {
