@@ -309,6 +309,7 @@ def main():
     ap.add_argument("--no-fp32", action="store_true", help="skip the FP32-flux variant")
     ap.add_argument("--fp32-only", action="store_true", help="time only the FP32-flux form (profiling runs)")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint variant")
+    ap.add_argument("--no-snapshot", action="store_true", help="skip the snapshot save/load timing")
     ap.add_argument("--configs-table", action="store_true", help="GPU FP64 / FP32-flux and oracle 1-thread / "
                     "all-thread rates for every workload of the config list (one JSON line each)")
     ap.add_argument("--paper-meshes", default="", help="comma list of the paper's meshes (A..I) to time "
@@ -420,6 +421,24 @@ def main():
     variants = {}
     if not args.no_fp32:
         solver32, r32 = timed_form(jz.JZ_PREC_FP32FLUX, False)
+        # flow statistics: one sample = one HBM sweep (read rho, rho u_x, mean, M2; write mean, M2)
+        solver32.stats_begin(0)
+        for _ in range(3):
+            solver32.stats_sample()
+        solver32.profile_read()
+        solver32.profile(True)
+        for _ in range(10):
+            solver32.stats_sample()
+        fs_ms, fs_n = solver32.profile_read()["stats"]
+        solver32.profile(False)
+        solver32.stats_end()
+        fs_per = fs_ms / fs_n
+        fs_gbs = 48.0 * npts / (fs_per / 1e3) / 1e9
+        variants["flow_stats"] = {
+            "kernel": "flow_sample", "ms_per_sample": fs_per, "samples": int(fs_n),
+            "roofline": {"bound": "hbm", "kernel": "flow_sample", "achieved": fs_gbs, "peak": hbm_peak,
+                         "unit": "GB/s", "frac": fs_gbs / hbm_peak, "traffic": None,
+                         "algorithmic_bytes_per_node": 48}}
         solver32.close()
         v32 = ws * npts * 5 * args.steps / (r32["ms"] / 1e3) / 1e9
         fms, fn = r32["prof"]["fused32"]
@@ -440,6 +459,29 @@ def main():
                                 "fields": ["rho", "rho_u", "rho_v", "rho_w", "e"]},
             "speedup_vs_fp64": v32 / value,
         }
+
+    # --- snapshots: save / load throughput on the 512 x 256 x 128 jet (671 MB of state) ---
+    if not args.no_snapshot and rank == 0:
+        import tempfile
+        gs, qs, ps = W.make_workload("jet512x256x128")
+        grid_s = jz.Grid.from_workload(gs)
+        ss = jz.Solver(grid_s, ps, jz.JZ_PREC_FP64, stream=stream.cuda_stream)
+        ss.set_state(torch.from_numpy(qs).cuda(), 0.0)
+        with tempfile.TemporaryDirectory() as tmp:
+            path = os.path.join(tmp, "snap.bin")
+            ss.save(path)                                   # warm-up (staging, page cache)
+            t0 = time.perf_counter()
+            ss.save(path)
+            t_save = time.perf_counter() - t0
+            t0 = time.perf_counter()
+            ss.load(path)
+            t_load = time.perf_counter() - t0
+            nbytes = os.path.getsize(path)
+        ss.close()
+        grid_s.close()
+        variants["snapshot"] = {"workload": "jet512x256x128", "bytes": nbytes, "save_s": t_save, "load_s": t_load,
+                                "save_gbs": nbytes / t_save / 1e9, "load_gbs": nbytes / t_load / 1e9,
+                                "note": "host file I/O through 64 MiB pinned chunks, FNV-1a hashed; page cache warm"}
 
     # --- discrete adjoint: dJ/dA on the 128 x 96 x 64 jet, 200 steps, checkpoints every 20 ---
     if not args.no_adjoint:

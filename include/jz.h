@@ -154,10 +154,15 @@ int jz_destroy(jz_solver* s);
 
 /* Set the state Q (Algorithm 2: Calc(I.C.) / restart) and time t.  q is
  * [5][N], host or device.  The state is taken as given (no boundary
- * condition is applied); ghost points are filled. */
+ * condition is applied); ghost points are filled.  Page-locked host memory
+ * is read by the packing kernel directly over the host link; other host
+ * memory goes through a device staging copy.  Host input: returns when the
+ * copy is done; device input: queued on the solver's stream. */
 int jz_set_state(jz_solver* s, const double* q, double t);
 
-/* Copy the current state to q [5][N], host or device. */
+/* Copy the current state to q [5][N], host or device (page-locked host
+ * memory is written by the unpacking kernel directly).  Host output:
+ * returns when the data is there; device output: queued on the stream. */
 int jz_get_state(jz_solver* s, double* q);
 
 /* One evaluation of RHS(q) of eq. vec-les (dQ/dt = -RHS) on every node the

@@ -45,6 +45,18 @@ bool is_device_ptr(const void* p) {
   return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+// Device-side address of page-locked host memory (cudaHostAlloc / cudaHostRegister,
+// mapped into the device's address space), or nullptr for other host memory.  Kernels
+// read and write such buffers directly over the host link, with no staging copy.
+void* pinned_view(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
 // Owner of a list of device allocations.
 struct DevMem {
   std::vector<void*> blocks;
@@ -148,15 +160,20 @@ int ensure_staging(jz_solver* s) {
 int load_state(jz_solver* s, const double* src, jz::State& q) {
   const jz::Dims& d = s->grid->d;
   const double* dev = src;
+  bool host = false;
   if (!is_device_ptr(src)) {
-    int r = ensure_staging(s);
-    if (r) return r;
-    JZ_CK(cudaMemcpyAsync(s->staging, src, 5 * sizeof(double) * npts(d), cudaMemcpyHostToDevice, s->st));
-    dev = s->staging;
+    host = true;
+    dev = static_cast<const double*>(pinned_view(src));   // page-locked: the pack kernel reads it
+    if (!dev) {                                           // pageable: staging copy
+      int r = ensure_staging(s);
+      if (r) return r;
+      JZ_CK(cudaMemcpyAsync(s->staging, src, 5 * sizeof(double) * npts(d), cudaMemcpyHostToDevice, s->st));
+      dev = s->staging;
+    }
   }
   JZ_CK(jz::pack_real(d, q.q, dev, 5, s->st));
   JZ_CK(jz::ghost_fill(d, q.q, 5, s->st));
-  if (dev == s->staging) JZ_CK(cudaStreamSynchronize(s->st));
+  if (host) JZ_CK(cudaStreamSynchronize(s->st));           // the caller may reuse its host buffer
   return JZ_OK;
 }
 
@@ -566,6 +583,11 @@ int jz_get_state(jz_solver* s, double* q) {
   const jz::Dims& d = s->grid->d;
   if (is_device_ptr(q)) {
     JZ_CK(jz::unpack_real(d, s->qn.q, q, 5, s->st));
+    return JZ_OK;
+  }
+  if (double* mapped = static_cast<double*>(pinned_view(q))) {   // page-locked: written directly
+    JZ_CK(jz::unpack_real(d, s->qn.q, mapped, 5, s->st));
+    JZ_CK(cudaStreamSynchronize(s->st));
     return JZ_OK;
   }
   int r = ensure_staging(s);

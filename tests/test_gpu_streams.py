@@ -67,3 +67,27 @@ def test_adjoint_on_side_stream(jz):
     # J and dJ/dA are sums with atomic additions: equal up to the order of those sums
     assert abs(Ja - Jb) <= 1e-12 * abs(Ja)
     assert np.abs(ga - gb).max() <= 1e-12 * np.abs(ga).max()
+
+
+def test_state_transfer_paths_agree(jz):
+    """jz_set_state / jz_get_state from and to device memory, page-locked host memory (read
+    and written by the packing kernels over the host link) and pageable host memory (staging
+    copy) move the same bytes."""
+    g = W.jet_grid(70, 34, 16)
+    q = W.jet_state(g) + 1e-3 * np.random.default_rng(3).standard_normal((5, g.nk, g.nj, g.ni))
+    prm = W.jet_params(seed=2)
+    grid = jz.Grid.from_workload(g)
+    s = jz.Solver(grid, prm, jz.JZ_PREC_FP64, stream=torch.cuda.Stream().cuda_stream)
+    sources = {"pageable": q, "pinned": torch.from_numpy(q).pin_memory(), "device": torch.from_numpy(q).cuda()}
+    outs = {}
+    for name, src in sources.items():
+        s.set_state(src, 0.0)
+        s.step(1, stats=False)
+        for oname, dst in (("pageable", np.empty_like(q)), ("pinned", torch.empty(q.shape, dtype=torch.float64).pin_memory()),
+                           ("device", torch.empty(q.shape, dtype=torch.float64, device="cuda"))):
+            s.get_state(dst)
+            torch.cuda.synchronize()
+            outs[(name, oname)] = dst.cpu().numpy() if isinstance(dst, torch.Tensor) else dst
+    ref = outs[("pageable", "pageable")]
+    for key, val in outs.items():
+        assert np.array_equal(val, ref), key
