@@ -44,9 +44,9 @@ FLOPS_PER_POINT = {"nodal": 83, "viscous": 233, "faces": 168, "update": 76}
 # dram__bytes_write.sum / nodes), scaled to the full launch by its node count;
 # profiles/k_viscous_fp64_jet256x128x64.md: (541.0 + 225.7) MB over 258 x 130 x 66 nodes.
 TRAFFIC_PER_NODE = {"viscous": 346.3}
-# k_fused32: (123 + 4 x 170) / 5 DRAM bytes per node over a step's five launches
+# k_fused32: (122.3 + 4 x 170.5) / 5 DRAM bytes per node over a step's five launches
 # (stage 1 and stage 2 captures of the current kernel in profiles/k_fused32_jet256x128x64.md).
-TRAFFIC_FUSED32_PER_NODE = (123.0 + 4 * 170.0) / 5
+TRAFFIC_FUSED32_PER_NODE = (122.3 + 4 * 170.5) / 5
 
 
 def _dist():
@@ -434,11 +434,15 @@ def main():
         solver32.stats_end()
         fs_per = fs_ms / fs_n
         fs_gbs = 48.0 * npts / (fs_per / 1e3) / 1e9
+        # FP64-pipe bound: 9 FP64 instructions per node against 2 per SM per clock
+        fs_inst = 9.0 * npts / (fs_per / 1e3) / 1e12
+        fs_peak = 152 * 2 * 2.07e9 / 1e12
         variants["flow_stats"] = {
             "kernel": "flow_sample", "ms_per_sample": fs_per, "samples": int(fs_n),
-            "roofline": {"bound": "hbm", "kernel": "flow_sample", "achieved": fs_gbs, "peak": hbm_peak,
-                         "unit": "GB/s", "frac": fs_gbs / hbm_peak, "traffic": None,
-                         "algorithmic_bytes_per_node": 48}}
+            "roofline": {"bound": "alu", "kernel": "flow_sample", "achieved": fs_inst, "peak": fs_peak,
+                         "unit": "T FP64-inst/s", "frac": fs_inst / fs_peak, "traffic": None,
+                         "fp64_inst_per_node": 9, "peak_source": "152 SMs x 2 FP64 inst/clk x 2.07 GHz"},
+            "hbm": {"achieved_gbs": fs_gbs, "frac": fs_gbs / hbm_peak, "algorithmic_bytes_per_node": 48}}
         solver32.close()
         v32 = ws * npts * 5 * args.steps / (r32["ms"] / 1e3) / 1e9
         fms, fn = r32["prof"]["fused32"]

@@ -502,12 +502,26 @@ int jz_create(jz_grid* g, const jz_params* p, void* stream, jz_solver** out) {
       A(tmp, 10);
       Sf_dev = reinterpret_cast<float**>(tmp);
     }
-    // CTAs of 30 x 8 columns; split k so that the grid covers the SMs evenly
+    // CTAs of 30 x 8 columns marching in k.  Split k into chunks so that the CTA count fills
+    // the resident slots evenly: minimise (waves) x (planes per CTA + the 3 priming planes).
     const int tx = jz::fused32_tile_x(), ty = jz::fused32_tile_y();
     const long long tiles = (long long)((d.ni + tx - 1) / tx) * ((d.nj + ty - 1) / ty);
-    int nch = 1;
-    while (tiles * nch < 8 * 304 && nch < d.nk / 16) nch *= 2;
-    s->kchunk = (d.nk + nch - 1) / nch;
+    int slots = 304;
+    if (jz::fused32_slots(&slots) != cudaSuccess) {
+      cudaGetLastError();
+      slots = 304;
+    }
+    int best = 1;
+    long long best_cost = -1;
+    for (int nch = 1; nch <= std::max(1, d.nk / 8); ++nch) {
+      const long long waves = (tiles * nch + slots - 1) / slots;
+      const long long cost = waves * ((d.nk + nch - 1) / nch + 3);
+      if (best_cost < 0 || cost < best_cost) {
+        best_cost = cost;
+        best = nch;
+      }
+    }
+    s->kchunk = (d.nk + best - 1) / best;
   } else {
     A(s->w.u, d.Np); A(s->w.v, d.Np); A(s->w.w, d.Np); A(s->w.T, d.Np); A(s->w.p, d.Np); A(s->w.mu, d.Np);
     for (int dir = 0; dir < 3; ++dir) {

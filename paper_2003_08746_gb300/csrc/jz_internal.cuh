@@ -217,6 +217,7 @@ cudaError_t update64(const Dims& d, const GridDev& g, const Work64& w, const Sta
 cudaError_t fused32(const Dims& d, const Consts& c, float* const* Sf, const State& qin, const State& qn,
                     const State& qout, Scalars* sc, double alpha, int want_res, int want_rate, double* rhs_flat,
                     int kchunk, cudaStream_t st);
+cudaError_t fused32_slots(int* slots);
 int fused32_tile_x();
 int fused32_tile_y();
 // boundary conditions (jet), in this order after every stage

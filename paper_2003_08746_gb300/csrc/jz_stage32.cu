@@ -585,19 +585,43 @@ __global__ void __launch_bounds__(NT, kMinBlocks) k_fused32(Args A) {
 
 }  // namespace
 
-cudaError_t fused32(const Dims& d, const Consts& c, float* const* Sf, const State& qin, const State& qn,
-                    const State& qout, Scalars* sc, double alpha, int want_res, int want_rate, double* rhs_flat,
-                    int kchunk, cudaStream_t st) {
-  static bool attr[64] = {false};     // the attribute is per device
-  const int smem = (int)sizeof(Smem);
+namespace {
+
+// The dynamic shared-memory size above 48 KB must be allowed once per device.
+cudaError_t allow_smem() {
+  static bool attr[64] = {false};
   int dev = 0;
   cudaError_t e0 = cudaGetDevice(&dev);
   if (e0 != cudaSuccess) return e0;
   if (dev < 0 || dev >= 64 || !attr[dev]) {
-    cudaError_t e = cudaFuncSetAttribute(k_fused32, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaError_t e = cudaFuncSetAttribute(k_fused32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Smem));
     if (e != cudaSuccess) return e;
     if (dev >= 0 && dev < 64) attr[dev] = true;
   }
+  return cudaSuccess;
+}
+
+}  // namespace
+
+// Resident CTAs of the fused kernel on the whole device (SMs x CTAs per SM).
+cudaError_t fused32_slots(int* slots) {
+  cudaError_t e = allow_smem();
+  if (e != cudaSuccess) return e;
+  int dev = 0, sms = 0, per = 0;
+  e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_fused32, NT, (int)sizeof(Smem));
+  if (e != cudaSuccess) return e;
+  *slots = sms * (per > 0 ? per : 1);
+  return cudaSuccess;
+}
+
+cudaError_t fused32(const Dims& d, const Consts& c, float* const* Sf, const State& qin, const State& qn,
+                    const State& qout, Scalars* sc, double alpha, int want_res, int want_rate, double* rhs_flat,
+                    int kchunk, cudaStream_t st) {
+  const int smem = (int)sizeof(Smem);
+  cudaError_t e0 = allow_smem();
+  if (e0 != cudaSuccess) return e0;
   Args A;
   A.d = d;
   A.c.gamma = (float)c.gamma; A.c.gm1 = (float)c.gm1; A.c.mu_ref = (float)c.mu_ref; A.c.S_hat = (float)c.S_hat;

@@ -8,8 +8,10 @@
 // M2 += (u - mean_old)(u - mean_new)), which stays accurate when the
 // fluctuations are many orders below the mean.  A sample reads rho and
 // rho u_x and rewrites both accumulators: 48 bytes per node, coalesced along
-// i, one HBM sweep.  The read-out averages mean and rms = sqrt(M2 / n) over
-// the azimuth k for every (i, j).
+// i, one sweep.  Its 9 FP64 instructions per node (reciprocal 4, product 1,
+// Welford update 4) at 2 per SM per clock take longer than the 48 bytes at
+// HBM speed, so the FP64 pipe bounds it.  The read-out averages mean and
+// rms = sqrt(M2 / n) over the azimuth k for every (i, j).
 #include "jz_internal.cuh"
 
 namespace jz {
@@ -24,7 +26,7 @@ __global__ void k_flow_sample(Dims d, const double* __restrict__ q0, const doubl
   const int j = blockIdx.y, k = blockIdx.z;
   const long long p = pidx(d, i, j, k);
   const long long t = ((long long)k * d.nj + j) * d.ni + i;
-  const double u = q1[p] / q0[p];
+  const double u = q1[p] * rcp64(q0[p]);       // the FP64 pipe, not HBM, bounds this kernel
   const double m = mean[t];
   const double dl = u - m;
   const double mn = m + dl * inv_n;
