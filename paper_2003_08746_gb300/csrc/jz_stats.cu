@@ -26,7 +26,9 @@ __global__ void k_flow_sample(Dims d, const double* __restrict__ q0, const doubl
   const int j = blockIdx.y, k = blockIdx.z;
   const long long p = pidx(d, i, j, k);
   const long long t = ((long long)k * d.nj + j) * d.ni + i;
-  const double u = q1[p] * rcp64(q0[p]);       // the FP64 pipe, not HBM, bounds this kernel
+  // one rounded product (never fused into the subtractions below, so that a single sample
+  // leaves M2 exactly 0); the FP64 pipe, not HBM, bounds this kernel
+  const double u = __dmul_rn(q1[p], rcp64(q0[p]));
   const double m = mean[t];
   const double dl = u - m;
   const double mn = m + dl * inv_n;
