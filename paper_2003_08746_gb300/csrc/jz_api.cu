@@ -45,6 +45,10 @@ bool is_device_ptr(const void* p) {
   return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+// Status for a failed device allocation: out of memory, or another CUDA error
+// (no device, driver too old, a sticky error from an earlier fault).
+int alloc_status(cudaError_t e) { return e == cudaErrorMemoryAllocation ? JZ_ERR_OOM : JZ_ERR_CUDA; }
+
 // Device-side address of page-locked host memory (cudaHostAlloc / cudaHostRegister,
 // mapped into the device's address space), or nullptr for other host memory.  Kernels
 // read and write such buffers directly over the host link, with no staging copy.
@@ -152,7 +156,7 @@ int ensure_staging(jz_solver* s) {
   if (s->staging) return JZ_OK;
   cudaError_t e;
   s->staging = s->mem.alloc(5 * (size_t)npts(s->grid->d), e, s->st);
-  if (!s->staging) return fail(JZ_ERR_OOM, "staging buffer: %s", cudaGetErrorString(e));
+  if (!s->staging) return fail(alloc_status(e), "staging buffer: %s", cudaGetErrorString(e));
   return JZ_OK;
 }
 
@@ -344,14 +348,14 @@ int jz_create_grid(int ni, int nj, int nk, const double* xyz, const double* peri
     *sl = g->mem64.alloc(d.Np, e, nullptr);
     if (!*sl || e != cudaSuccess) {
       delete g;
-      return fail(JZ_ERR_OOM, "grid arrays: %s", cudaGetErrorString(e));
+      return fail(alloc_status(e), "grid arrays: %s", cudaGetErrorString(e));
     }
   }
   g->g.Sb = g->mem.alloc(3 * (size_t)d.nk * d.ni, e, nullptr);
   if (e == cudaSuccess) g->g.Xin = g->mem.alloc(2 * (size_t)d.nk * d.nj, e, nullptr);
   if (e != cudaSuccess) {
     delete g;
-    return fail(JZ_ERR_OOM, "grid surface arrays: %s", cudaGetErrorString(e));
+    return fail(alloc_status(e), "grid surface arrays: %s", cudaGetErrorString(e));
   }
   const long long N = npts(d);
   // coordinates already on the device are padded in place; host ones go through a staging copy
@@ -361,7 +365,7 @@ int jz_create_grid(int ni, int nj, int nk, const double* xyz, const double* peri
     e = cudaMalloc(&tmp, 3 * sizeof(double) * N);
     if (e != cudaSuccess) {
       delete g;
-      return fail(JZ_ERR_OOM, "coordinate staging: %s", cudaGetErrorString(e));
+      return fail(alloc_status(e), "coordinate staging: %s", cudaGetErrorString(e));
     }
     e = cudaMemcpy(tmp, xyz, 3 * sizeof(double) * N, cudaMemcpyHostToDevice);
     src = tmp;
@@ -391,7 +395,7 @@ int jz_compute_metrics(jz_grid* g) {
   cudaError_t e;
   for (int i = 0; i < 9; ++i) {
     s9[i] = scratch.alloc(d.Np, e, nullptr);
-    if (!s9[i]) return fail(JZ_ERR_OOM, "metric scratch: %s", cudaGetErrorString(e));
+    if (!s9[i]) return fail(alloc_status(e), "metric scratch: %s", cudaGetErrorString(e));
   }
   int* bad = nullptr;
   JZ_CK(cudaMalloc(&bad, sizeof(int)));
@@ -420,7 +424,7 @@ int jz_grid_compact(jz_grid* g) {
     Sf[i] = reinterpret_cast<float*>(g->mem.alloc((d.Np + 1) / 2, e, nullptr));
   float** table = nullptr;
   if (e == cudaSuccess) table = reinterpret_cast<float**>(g->mem.alloc(10, e, nullptr));
-  if (e != cudaSuccess) return fail(JZ_ERR_OOM, "jz_grid_compact: %s", cudaGetErrorString(e));
+  if (e != cudaSuccess) return fail(alloc_status(e), "jz_grid_compact: %s", cudaGetErrorString(e));
   JZ_CK(cudaMemcpy(table, Sf, sizeof Sf, cudaMemcpyHostToDevice));
   JZ_CK(jz::metrics_to_f32(d, g->g, table, nullptr));
   JZ_CK(cudaDeviceSynchronize());
@@ -543,7 +547,7 @@ int jz_create(jz_grid* g, const jz_params* p, void* stream, jz_solver** out) {
   }
   if (e != cudaSuccess) {
     delete s;
-    return fail(JZ_ERR_OOM, "jz_create: device allocation failed: %s", cudaGetErrorString(e));
+    return fail(alloc_status(e), "jz_create: device allocation failed: %s", cudaGetErrorString(e));
   }
   if (s->fp32 && Sf_dev) {
     e = cudaMemcpyAsync(Sf_dev, s->Sf, sizeof(s->Sf), cudaMemcpyHostToDevice, s->st);
@@ -743,7 +747,7 @@ int jz_adjoint_step(jz_solver* s, const double* forcing_amps, int nsteps, int ck
   for (auto& st : seg) AS(st);
   for (auto& st : stg) AS(st);
   AS(wa); AS(wb);
-  if (e != cudaSuccess) return fail(JZ_ERR_OOM, "jz_adjoint_step: device allocation failed: %s", cudaGetErrorString(e));
+  if (e != cudaSuccess) return fail(alloc_status(e), "jz_adjoint_step: device allocation failed: %s", cudaGetErrorString(e));
   JZ_CK(cudaMemcpyAsync(wdev, w.data(), sizeof(double) * d.ni, cudaMemcpyHostToDevice, s->st));
   // frozen time step and start time
   if (s->c.dt_fixed <= 0.0) JZ_RUN(JZ_PROF_REDUCE, jz::cfl_rate(d, s->c, g, s->qn, s->sc, s->st));
@@ -1012,7 +1016,7 @@ int jz_stats_begin(jz_solver* s, int every) {
   if (e == cudaSuccess) e = cudaMalloc(&s->fs_out, 2 * P * sizeof(double));
   if (e != cudaSuccess) {
     s->free_stats();
-    return fail(JZ_ERR_OOM, "jz_stats_begin: %s", cudaGetErrorString(e));
+    return fail(alloc_status(e), "jz_stats_begin: %s", cudaGetErrorString(e));
   }
   JZ_CK(cudaMemsetAsync(s->fs_mean, 0, N * sizeof(double), s->st));
   JZ_CK(cudaMemsetAsync(s->fs_m2, 0, N * sizeof(double), s->st));

@@ -81,7 +81,8 @@ def test_single_sample_exact(jz):
     mean, rms, n = s.stats_read()
     Q = s.get_state()
     assert n == 1 and np.all(rms == 0.0)
-    assert np.abs(mean - (Q[1] / Q[0]).mean(axis=0)).max() <= 1e-15
+    # u_x by the library's reciprocal (about 1 ulp) and summed in another order: a few ulp of U_j
+    assert np.abs(mean - (Q[1] / Q[0]).mean(axis=0)).max() <= 1e-14
     # restart: begin again clears the accumulators
     s.stats_begin(1)
     s.step(2, stats=False)
