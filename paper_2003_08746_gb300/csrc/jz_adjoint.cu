@@ -39,8 +39,8 @@ __device__ __forceinline__ bool advanced(const Dims& d, int i, int j) {
 
 // Reverse of u_i = m_i / rho, p = (gamma-1)(e - m.u/2) at one node: adds to qb.
 __device__ __forceinline__ void prim_bar(const Consts& c, const double q[5], double ub[3], double pb, double qb[5]) {
-  const double rho = q[0];
-  const double u[3] = {q[1] / rho, q[2] / rho, q[3] / rho};
+  const double ir = rcp64(q[0]);
+  const double u[3] = {q[1] * ir, q[2] * ir, q[3] * ir};
   qb[4] += c.gm1 * pb;
   const double keb = -c.gm1 * pb;
   for (int a = 0; a < 3; ++a) {
@@ -49,10 +49,10 @@ __device__ __forceinline__ void prim_bar(const Consts& c, const double q[5], dou
   }
   double s = 0.0;
   for (int a = 0; a < 3; ++a) {
-    qb[1 + a] += ub[a] / rho;
+    qb[1 + a] += ub[a] * ir;
     s += ub[a] * u[a];
   }
-  qb[0] += -s / rho;
+  qb[0] += -s * ir;
 }
 
 __device__ __forceinline__ void load5(const State& q, long long p, double v[5]) {
@@ -148,9 +148,10 @@ __global__ void k_adj_visc(Dims d, Consts c, GridDev g, Work64 w, State q, Adj64
   const double mu_sgs = rho * (csd * csd) * Smod;
   const double mu_eff = mu + mu_sgs;
   const double k_eff = mu * c.k_lam + mu_sgs * c.k_sgs;
+  const double d3 = div * (1.0 / 3.0);
   double tau[3][3];
   for (int x = 0; x < 3; ++x)
-    for (int y = 0; y < 3; ++y) tau[x][y] = 2.0 * mu_eff * (Sij[x][y] - (x == y ? div / 3.0 : 0.0));
+    for (int y = 0; y < 3; ++y) tau[x][y] = 2.0 * mu_eff * (Sij[x][y] - (x == y ? d3 : 0.0));
   const double vel[3] = {w.u[p], w.v[p], w.w[p]};
   // reverse: F^dir_m = S^dir_j F_j,m ; H = E - F
   double Fb[3][4];
@@ -171,16 +172,16 @@ __global__ void k_adj_visc(Dims d, Consts c, GridDev g, Work64 w, State q, Adj64
   double mueb = 0.0, Sijb[3][3], divb = 0.0;
   for (int x = 0; x < 3; ++x)
     for (int y = 0; y < 3; ++y) {
-      mueb += taub[x][y] * 2.0 * (Sij[x][y] - (x == y ? div / 3.0 : 0.0));
+      mueb += taub[x][y] * 2.0 * (Sij[x][y] - (x == y ? d3 : 0.0));
       Sijb[x][y] = 2.0 * mu_eff * taub[x][y];
     }
-  for (int x = 0; x < 3; ++x) divb += -(2.0 * mu_eff / 3.0) * taub[x][x];
+  for (int x = 0; x < 3; ++x) divb += -(mu_eff * (2.0 / 3.0)) * taub[x][x];
   for (int x = 0; x < 3; ++x) Sijb[x][x] += divb;
   const double mub = keb * c.k_lam + mueb;
   const double musb = keb * c.k_sgs + mueb;
   const double rhob = musb * (csd * csd) * Smod;
   const double Smodb = musb * rho * (csd * csd);
-  const double SSb = Smod > 0.0 ? Smodb / Smod : 0.0;
+  const double SSb = Smod > 0.0 ? Smodb * rcp64(Smod) : 0.0;
   for (int x = 0; x < 3; ++x)
     for (int y = 0; y < 3; ++y) Sijb[x][y] += 2.0 * Sij[x][y] * SSb;
   double Lb[4][3];
@@ -199,9 +200,10 @@ __global__ void k_adj_visc(Dims d, Consts c, GridDev g, Work64 w, State q, Adj64
     const double nub = a.nb0[dir][p] + a.nb1[dir][p - s[dir]];
     const double pp = w.p[p + s[dir]], pm = w.p[p - s[dir]];
     const double N = pp - 2.0 * pc + pm, Dn = pp + 2.0 * pc + pm;
-    const double nu = fabs(N) / Dn;
-    a.cpm[dir][p] = nub * (sgn(N) - nu) / Dn;
-    a.c0[dir][p] = nub * (-2.0 * sgn(N) - 2.0 * nu) / Dn;
+    const double iD = rcp64(Dn);
+    const double nu = fabs(N) * iD;
+    a.cpm[dir][p] = nub * (sgn(N) - nu) * iD;
+    a.c0[dir][p] = nub * (-2.0 * sgn(N) - 2.0 * nu) * iD;
   }
 }
 
@@ -243,11 +245,13 @@ __global__ void k_adj_nodal(Dims d, Consts c, GridDev g, Work64 w, State q, Adj6
   double Q[5];
   load5(q, p, Q);
   const double rho = Q[0];
-  const double u[3] = {Q[1] / rho, Q[2] / rho, Q[3] / rho};
+  const double ir = rcp64(rho);
+  const double u[3] = {Q[1] * ir, Q[2] * ir, Q[3] * ir};
   const double pr = c.gm1 * (Q[4] - 0.5 * (Q[1] * u[0] + Q[2] * u[1] + Q[3] * u[2]));
-  const double T = c.gamma * pr / rho;
+  const double T = c.gamma * pr * ir;
   const double aa = sqrt(T);
-  const double mu = c.mu_ref * (T * aa) * c.sut_num / (T + c.S_hat);
+  const double iTS = rcp64(T + c.S_hat);
+  const double mu = c.mu_ref * (T * aa) * c.sut_num * iTS;
   double Sv[3][3], Smag[3], U[3], lam[3];
   for (int dir = 0; dir < 3; ++dir) {
     for (int cc = 0; cc < 3; ++cc) Sv[dir][cc] = g.S[3 * dir + cc][p];
@@ -261,10 +265,10 @@ __global__ void k_adj_nodal(Dims d, Consts c, GridDev g, Work64 w, State q, Adj6
     double lo[3], hi[3], dlo[3], dhi[3];
     for (int dd = 0; dd < 3; ++dd) {
       if (c.sigma_is_two_thirds) {
-        const double t = cbrt(lam[dd]);
+        const double t = cbrt64(lam[dd]);
         lo[dd] = t;
         hi[dd] = t * t;
-        dlo[dd] = t != 0.0 ? 1.0 / (3.0 * t * t) : 0.0;      // d t / d lam
+        dlo[dd] = t != 0.0 ? rcp64(3.0 * t * t) : 0.0;      // d t / d lam
         dhi[dd] = 2.0 * t * dlo[dd];                        // d t^2 / d lam
       } else {
         const bool pos = lam[dd] > 0.0;
@@ -303,10 +307,10 @@ __global__ void k_adj_nodal(Dims d, Consts c, GridDev g, Work64 w, State q, Adj6
     for (int x = 0; x < 3; ++x) ub[x] += Ub[dir] * Sv[dir][x];
   }
   // Sutherland mu(T): d mu / dT = mu (1.5/T - 1/(T + S))
-  Tb += mub * mu * (1.5 / T - 1.0 / (T + c.S_hat));
-  Tb += ab / (2.0 * aa);
-  pb += Tb * c.gamma / rho;
-  qb[0] += -Tb * T / rho;
+  Tb += mub * mu * (1.5 * rcp64(T) - iTS);
+  Tb += ab * 0.5 * rcp64(aa);
+  pb += Tb * c.gamma * ir;
+  qb[0] += -Tb * T * ir;
   prim_bar(c, Q, ub, pb, qb);
   for (int m = 0; m < 5; ++m) a.lam[m][p] = qb[m];
 }
