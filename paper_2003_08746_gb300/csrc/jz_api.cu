@@ -141,7 +141,16 @@ struct jz_solver {
     fs_n = 0;
     fs_every = 0;
   }
+  // two-step CUDA graphs of jz_rk_step, keyed by the Q^n buffer they start from
+  cudaStream_t cap_st = nullptr;           // private stream used only for capturing
+  cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+  const double* gkey[2] = {nullptr, nullptr};
+  long long glaunch[2][JZ_NPROF] = {};     // kernel launches inside each graph, by kind
+  bool graphs_off = false;
   ~jz_solver() {
+    for (cudaGraphExec_t g : gexec)
+      if (g) cudaGraphExecDestroy(g);
+    if (cap_st) cudaStreamDestroy(cap_st);
     free_stats();
     for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
     for (cudaEvent_t e : ev_marks) cudaEventDestroy(e);
@@ -255,6 +264,70 @@ int run_step(jz_solver* s) {
   JZ_RUN(JZ_PROF_REDUCE, jz::set_dt(s->c, s->sc, 1, s->st));
   s->steps += 1;
   s->rate_ready = s->fp32 && s->c.dt_fixed <= 0.0;
+  return JZ_OK;
+}
+
+// Two time steps replayed as one CUDA graph.  A step launches 27 (FP32-flux form) or 43
+// (FP64 form) small kernels whose parameters never change between steps, except that the
+// roles of the Q^n and stage buffers swap every step and come back after two; so two steps
+// are captured once per starting buffer (on a private stream, nothing executes while
+// capturing) and replayed with one launch.  Not used while profiling (events between
+// kernels), while flow statistics are sampled, or before the FP32-flux form has a CFL rate.
+// Any capture failure turns graphs off for the solver; the steps then run as plain launches.
+int graph_two_steps(jz_solver* s, bool* done) {
+  *done = false;
+  if (s->graphs_off || s->prof || s->fs_every > 0) return JZ_OK;
+  if (s->fp32 && s->c.dt_fixed <= 0.0 && !s->rate_ready) return JZ_OK;
+  int slot = s->gkey[0] == s->qn.q[0] ? 0 : (s->gkey[1] == s->qn.q[0] ? 1 : -1);
+  if (slot < 0) {
+    slot = s->gexec[0] ? 1 : 0;
+    if (s->gexec[slot]) {
+      cudaGraphExecDestroy(s->gexec[slot]);
+      s->gexec[slot] = nullptr;
+      s->gkey[slot] = nullptr;
+    }
+    if (!s->cap_st && cudaStreamCreateWithFlags(&s->cap_st, cudaStreamNonBlocking) != cudaSuccess) {
+      cudaGetLastError();
+      s->graphs_off = true;
+      return JZ_OK;
+    }
+    // capture with the host bookkeeping saved, then restore it (nothing ran)
+    const jz::State qn = s->qn, qa = s->qa, qb = s->qb;
+    const long long steps = s->steps;
+    const bool rate_ready = s->rate_ready;
+    long long launches[JZ_NPROF];
+    std::memcpy(launches, s->launches, sizeof launches);
+    cudaStream_t user = s->st;
+    s->st = s->cap_st;
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(s->cap_st, cudaStreamCaptureModeThreadLocal);
+    int r = JZ_OK;
+    if (e == cudaSuccess) {
+      r = run_step(s);
+      if (r == JZ_OK) r = run_step(s);
+      e = cudaStreamEndCapture(s->cap_st, &graph);
+    }
+    s->st = user;
+    for (int k = 0; k < JZ_NPROF; ++k) s->glaunch[slot][k] = s->launches[k] - launches[k];
+    std::memcpy(s->launches, launches, sizeof launches);
+    s->qn = qn; s->qa = qa; s->qb = qb;
+    s->steps = steps;
+    s->rate_ready = rate_ready;
+    if (e == cudaSuccess && r == JZ_OK && graph) e = cudaGraphInstantiate(&s->gexec[slot], graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    if (e != cudaSuccess || r != JZ_OK || !s->gexec[slot]) {
+      cudaGetLastError();
+      s->gexec[slot] = nullptr;
+      s->graphs_off = true;
+      return JZ_OK;
+    }
+    s->gkey[slot] = s->qn.q[0];
+  }
+  JZ_CK(cudaGraphLaunch(s->gexec[slot], s->st));
+  for (int k = 0; k < JZ_NPROF; ++k) s->launches[k] += s->glaunch[slot][k];
+  s->steps += 2;
+  s->rate_ready = s->fp32 && s->c.dt_fixed <= 0.0;
+  *done = true;
   return JZ_OK;
 }
 
@@ -654,9 +727,19 @@ int jz_rk_step(jz_solver* s, int nsteps, jz_step_stats* out) {
     int r = mark(s, -1);
     if (r) return r;
   }
-  for (int n = 0; n < nsteps; ++n) {
+  for (int n = 0; n < nsteps;) {
+    if (nsteps - n >= 2) {
+      bool done = false;
+      int r = graph_two_steps(s, &done);
+      if (r) return r;
+      if (done) {
+        n += 2;
+        continue;
+      }
+    }
     int r = run_step(s);
     if (r) return r;
+    ++n;
     if (s->fs_every > 0 && s->steps % s->fs_every == 0) {
       r = stats_sample(s);
       if (r) return r;

@@ -91,3 +91,26 @@ def test_state_transfer_paths_agree(jz):
     ref = outs[("pageable", "pageable")]
     for key, val in outs.items():
         assert np.array_equal(val, ref), key
+
+
+@pytest.mark.parametrize("prec_name", ["JZ_PREC_FP64", "JZ_PREC_FP32FLUX"])
+def test_step_graphs_match_plain_launches(jz, prec_name):
+    """jz_rk_step replays pairs of steps as a CUDA graph; with profiling on it launches every
+    kernel itself.  Both give the same bits, for even and odd step counts, across calls and
+    after jz_set_state."""
+    prec = getattr(jz, prec_name)
+    g, q, prm = W.make_workload("box32x24x16")
+    grid = jz.Grid.from_workload(g)
+    plain = jz.Solver(grid, prm, prec)
+    plain.profile(True)                          # events between kernels: no graphs
+    graph = jz.Solver(grid, prm, prec, stream=torch.cuda.Stream().cuda_stream)
+    for s in (plain, graph):
+        s.set_state(q, 0.0)
+    for n in (1, 4, 7, 2):
+        a, b = plain.step(n), graph.step(n)
+        assert a.t == b.t and a.steps == b.steps
+        assert np.array_equal(plain.get_state(), graph.get_state()), n
+    for s in (plain, graph):
+        s.set_state(q, 0.0)
+    a, b = plain.step(6), graph.step(6)
+    assert np.array_equal(plain.get_state(), graph.get_state()) and a.t == b.t
