@@ -134,7 +134,6 @@ struct Phases {
 __global__ void k_build_inflow(Dims d, Consts c, GridDev g, double* u0, double* Gf, Phases ph) {
   const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (t >= (long long)d.nj * d.nk) return;
-  const int j = (int)(t % d.nj), k = (int)(t / d.nj);
   const double y = g.Xin[t], z = g.Xin[(long long)d.nj * d.nk + t];   // t = k nj + j
   const double r = sqrt(y * y + z * z);
   const double th = atan2(z, y);

@@ -53,7 +53,7 @@ constexpr int X_HX = 0, X_HY = 5, X_LX = 10, X_LY = 11, X_NX = 12, X_NY = 13, NX
 // zeta ring (tile): H^zeta(5), Lambda^zeta, nu^zeta, 1/V
 constexpr int Z_HZ = 0, Z_L = 5, Z_N = 6, Z_IV = 7, NZF = 8;
 // xi faces: TY rows of TX+1; eta faces: TY+1 rows of TX
-constexpr int NFX = TY * (TX + 1), NFY = (TY + 1) * TX, NFACE = NFX + NFY;
+constexpr int NFX = TY * (TX + 1), NFY = (TY + 1) * TX;
 
 struct Smem {
   float prim[NRING][NPF][NP2];
