@@ -281,12 +281,12 @@ def run_paper_meshes(args, jz, W, torch):
             row["fp64"]["grid"] = "full"
         free, _ = torch.cuda.mem_get_info()
         mode = "full"
-        if 160 * padded + 40 * npts + 24 * npts > 0.9 * free:
-            grid.compact()                           # frees 104 B per padded node
+        if 168 * padded + 40 * npts + 24 * npts > 0.9 * free:
+            grid.compact()                           # frees 96 B per padded node
             torch.cuda.empty_cache()
             mode = "compact"
         free, _ = torch.cuda.mem_get_info()
-        if (160 if mode == "full" else 120) * padded + 64 * npts < 0.9 * free:
+        if (168 if mode == "full" else 120) * padded + 64 * npts < 0.9 * free:
             row["fp32flux"] = timed(jz.JZ_PREC_FP32FLUX)
             row["fp32flux"]["grid"] = mode
         grid.close()

@@ -134,7 +134,7 @@ int jz_get_metrics(const jz_grid* g, double* out);
 /* Compact a grid for the FP32-flux form (no counterpart in the paper; it
  * lets one GPU hold the paper's largest mesh, 1700 x 1700 x 361 points).
  * The metrics are converted to FP32 once and kept by the grid (S^xi, S^eta,
- * S^zeta, V: 40 bytes per padded node), the far-field normals and the
+ * S^zeta, V, 1/V, V^(1/3): 48 bytes per padded node), the far-field normals and the
  * entrance-plane coordinates stay in FP64 surface arrays, and the FP64
  * coordinates and metrics (144 bytes per padded node) are freed.
  * Afterwards: FP32-flux solvers use the grid's FP32 metrics instead of their

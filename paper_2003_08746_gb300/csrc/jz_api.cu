@@ -108,7 +108,7 @@ struct jz_solver {
   jz::State qn{}, qa{}, qb{};
   jz::Work64 w{};
   bool fp32 = false;              // JZ_PREC_FP32FLUX form
-  float* Sf[10] = {nullptr};      // FP32 metrics (FP32-flux form)
+  const float* Mf = nullptr;      // FP32 metric records (FP32-flux form; the grid's if compact)
   int kchunk = 0;                 // k planes per CTA of the fused kernel
   bool rate_ready = false;        // a CFL rate of Q^n is in Scalars::rate_max
   jz::Scalars* sc = nullptr;
@@ -244,7 +244,7 @@ int run_step(jz_solver* s) {
     jz::State out = (l % 2 == 0) ? s->qa : s->qb;
     int r = JZ_OK;
     if (s->fp32)
-      JZ_RUN(JZ_PROF_FUSED32, jz::fused32(d, s->c, s->Sf, in, s->qn, out, s->sc, kAlpha[l], l == 0,
+      JZ_RUN(JZ_PROF_FUSED32, jz::fused32(d, s->c, s->Mf, in, s->qn, out, s->sc, kAlpha[l], l == 0,
                                           l == 4 && s->c.dt_fixed <= 0.0, nullptr, s->kchunk, s->st));
     else
       r = run_stage64(s, in, out, kAlpha[l], l == 0, nullptr);
@@ -492,20 +492,15 @@ int jz_grid_compact(jz_grid* g) {
   if (g->nsolvers > 0) return fail(JZ_ERR_STATE, "jz_grid_compact: %d solver(s) still use the grid", g->nsolvers);
   const jz::Dims& d = g->d;
   cudaError_t e = cudaSuccess;
-  float* Sf[10];
-  for (int i = 0; i < 10 && e == cudaSuccess; ++i)
-    Sf[i] = reinterpret_cast<float*>(g->mem.alloc((d.Np + 1) / 2, e, nullptr));
-  float** table = nullptr;
-  if (e == cudaSuccess) table = reinterpret_cast<float**>(g->mem.alloc(10, e, nullptr));
+  float* Mf = reinterpret_cast<float*>(g->mem.alloc((size_t)d.Np * jz::kMF / 2, e, nullptr));
   if (e != cudaSuccess) return fail(alloc_status(e), "jz_grid_compact: %s", cudaGetErrorString(e));
-  JZ_CK(cudaMemcpy(table, Sf, sizeof Sf, cudaMemcpyHostToDevice));
-  JZ_CK(jz::metrics_to_f32(d, g->g, table, nullptr));
+  JZ_CK(jz::metrics_to_f32(d, g->g, Mf, nullptr));
   JZ_CK(cudaDeviceSynchronize());
   g->mem64.release();
   for (int c = 0; c < 3; ++c) g->g.xyz[c] = g->g.Smag[c] = nullptr;
   for (int c = 0; c < 9; ++c) g->g.S[c] = nullptr;
   g->g.V = g->g.invV = g->g.Delta = nullptr;
-  for (int i = 0; i < 10; ++i) g->g.Sf[i] = Sf[i];
+  g->g.Mf = Mf;
   g->g.compact = 1;
   return JZ_OK;
 }
@@ -565,19 +560,15 @@ int jz_create(jz_grid* g, const jz_params* p, void* stream, jz_solver** out) {
     A(s->qb.q[m], d.Np);
   }
   s->fp32 = p->precision == JZ_PREC_FP32FLUX;
-  float** Sf_dev = nullptr;
+  float* own_mf = nullptr;
   if (s->fp32) {
     if (g->g.compact) {
-      for (int i = 0; i < 10; ++i) s->Sf[i] = const_cast<float*>(g->g.Sf[i]);   // the grid's own
+      s->Mf = g->g.Mf;                     // the grid's own records
     } else {
-      for (int i = 0; i < 10; ++i) {
-        double* tmp = nullptr;
-        A(tmp, (d.Np + 1) / 2);            // Np floats
-        s->Sf[i] = reinterpret_cast<float*>(tmp);
-      }
       double* tmp = nullptr;
-      A(tmp, 10);
-      Sf_dev = reinterpret_cast<float**>(tmp);
+      A(tmp, (size_t)d.Np * jz::kMF / 2);  // kMF floats per padded node
+      own_mf = reinterpret_cast<float*>(tmp);
+      s->Mf = own_mf;
     }
     // CTAs of 30 x 8 columns marching in k.  Split k into chunks so that the CTA count fills
     // the resident slots evenly: minimise (waves) x (planes per CTA + the 3 priming planes).
@@ -622,9 +613,8 @@ int jz_create(jz_grid* g, const jz_params* p, void* stream, jz_solver** out) {
     delete s;
     return fail(alloc_status(e), "jz_create: device allocation failed: %s", cudaGetErrorString(e));
   }
-  if (s->fp32 && Sf_dev) {
-    e = cudaMemcpyAsync(Sf_dev, s->Sf, sizeof(s->Sf), cudaMemcpyHostToDevice, s->st);
-    if (e == cudaSuccess) e = jz::metrics_to_f32(d, g->g, Sf_dev, s->st);
+  if (own_mf) {
+    e = jz::metrics_to_f32(d, g->g, own_mf, s->st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s->st);
     if (e != cudaSuccess) {
       delete s;
@@ -706,7 +696,7 @@ int jz_residual(jz_solver* s, const double* q, double* rhs) {
     if (r) return r;
   }
   if (s->fp32) {
-    JZ_RUN(JZ_PROF_FUSED32, jz::fused32(d, s->c, s->Sf, s->qb, s->qb, s->qb, s->sc, 0.0, 0, 0, dst, s->kchunk,
+    JZ_RUN(JZ_PROF_FUSED32, jz::fused32(d, s->c, s->Mf, s->qb, s->qb, s->qb, s->sc, 0.0, 0, 0, dst, s->kchunk,
                                         s->st));
   } else {
     r = run_stage64(s, s->qb, s->qb, 0.0, 0, dst);

@@ -172,10 +172,16 @@ __global__ void k_ghost_fill(Dims d, Ptrs16 f, int nvar) {
   for (int v = 0; v < nvar; ++v) f.p[v][p] = f.p[v][q];
 }
 
-__global__ void k_to_f32(Dims d, Ptrs16 src, float* const* dst, int nvar) {
+// FP32 metric records: kMF floats per padded node from kMF FP64 arrays.
+__global__ void k_to_f32(Dims d, Ptrs16 src, float* __restrict__ dst) {
   const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (t >= d.Np) return;
-  for (int v = 0; v < nvar; ++v) dst[v][t] = __double2float_rn(src.p[v][t]);
+  float r[kMF];
+  for (int v = 0; v < kMF; ++v) r[v] = __double2float_rn(src.p[v][t]);
+  float4* o = reinterpret_cast<float4*>(dst + t * kMF);
+  o[0] = make_float4(r[0], r[1], r[2], r[3]);
+  o[1] = make_float4(r[4], r[5], r[6], r[7]);
+  o[2] = make_float4(r[8], r[9], r[10], r[11]);
 }
 
 __global__ void k_pack(Dims d, Ptrs16 padded, const double* __restrict__ flat, int nvar) {
@@ -283,11 +289,13 @@ cudaError_t boundary_copies(const Dims& d, const GridDev& g, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-cudaError_t metrics_to_f32(const Dims& d, const GridDev& g, float* const* dst_dev, cudaStream_t st) {
-  double* M[10];
+cudaError_t metrics_to_f32(const Dims& d, const GridDev& g, float* Mf, cudaStream_t st) {
+  double* M[kMF];
   for (int i = 0; i < 9; ++i) M[i] = g.S[i];
-  M[9] = g.V;
-  k_to_f32<<<blocks_for(d.Np, kTPB), kTPB, 0, st>>>(d, ptrs(M, 10), dst_dev, 10);
+  M[MF_V] = g.V;
+  M[MF_IV] = g.invV;
+  M[MF_D] = g.Delta;
+  k_to_f32<<<blocks_for(d.Np, kTPB), kTPB, 0, st>>>(d, ptrs(M, kMF), Mf);
   return cudaGetLastError();
 }
 

@@ -93,8 +93,13 @@ struct GridDev {
   // compact grids (jz_grid_compact): the FP64 arrays above except Sb and Xin are
   // released and the metrics are kept in FP32 only
   int compact;
-  const float* Sf[10];  // S^xi, S^eta, S^zeta (9), V in FP32 (compact grids)
+  const float* Mf;    // compact grids: the FP32 metric records (kMF floats per padded node)
 };
+
+// FP32 metric record of one padded node (the FP32-flux form): S^xi, S^eta, S^zeta (9),
+// V, 1/V (0 where V = 0), V^(1/3); 48 bytes, read as three 16-byte vectors.
+constexpr int kMF = 12;
+constexpr int MF_V = 9, MF_IV = 10, MF_D = 11;
 
 // Derived constants of the non-dimensional formulation, by value.
 struct Consts {
@@ -197,7 +202,7 @@ cudaError_t compute_metrics(const Dims& d, GridDev& g, double* scratch9[9], cuda
 cudaError_t ghost_fill(const Dims& d, double* const* f, int nvar, cudaStream_t st);
 // FP32 copy of the metrics S (9) and V; dst_dev is a device array of 10 pointers
 cudaError_t boundary_copies(const Dims& d, const GridDev& g, cudaStream_t st);
-cudaError_t metrics_to_f32(const Dims& d, const GridDev& g, float* const* dst_dev, cudaStream_t st);
+cudaError_t metrics_to_f32(const Dims& d, const GridDev& g, float* Mf, cudaStream_t st);
 // copy between unpadded [nvar][N] and padded real region
 cudaError_t pack_real(const Dims& d, double* const* padded, const double* flat, int nvar,
                       cudaStream_t st);
@@ -213,8 +218,8 @@ cudaError_t faces64(const Dims& d, const Consts& c, const Work64& w, const State
 cudaError_t update64(const Dims& d, const GridDev& g, const Work64& w, const State& qin, const State& qn,
                      const State& qout, const Scalars* sc, double alpha, int want_res, double* rhs_flat,
                      cudaStream_t st);
-// FP32-flux stage (one fused kernel); Sf = FP32 metrics S (9) and V.
-cudaError_t fused32(const Dims& d, const Consts& c, float* const* Sf, const State& qin, const State& qn,
+// FP32-flux stage (one fused kernel); Mf = the FP32 metric records (kMF floats per padded node).
+cudaError_t fused32(const Dims& d, const Consts& c, const float* Mf, const State& qin, const State& qn,
                     const State& qout, Scalars* sc, double alpha, int want_res, int want_rate, double* rhs_flat,
                     int kchunk, cudaStream_t st);
 cudaError_t fused32_slots(int* slots);

@@ -36,13 +36,13 @@ __global__ void k_cfl_rate(Dims d, GridDev g, State q, Consts c, Scalars* sc) {
       rate = lsum * g.invV[p];
     } else {
       // compact grid: the same rate from the FP32 metrics, widened
+      const float* M = g.Mf + p * kMF;
       for (int dir = 0; dir < 3; ++dir) {
-        const double sx = g.Sf[3 * dir][p], sy = g.Sf[3 * dir + 1][p], sz = g.Sf[3 * dir + 2][p];
+        const double sx = M[3 * dir], sy = M[3 * dir + 1], sz = M[3 * dir + 2];
         const double lam = fabs(sx * u + sy * v + sz * w) + a * sqrt(sx * sx + sy * sy + sz * sz);
         lsum = dir == 0 ? lam : lsum + lam;
       }
-      const double V = g.Sf[9][p];
-      rate = V > 0.0 ? lsum / V : 0.0;
+      rate = lsum * (double)M[MF_IV];
     }
   }
   __shared__ double red[kTPB / 32];
@@ -81,7 +81,7 @@ __global__ void k_stats_partial(Dims d, GridDev g, State q, Consts c, double* pa
     const long long r = t / d.ni;
     const int j = (int)(r % d.nj), k = (int)(r / d.nj);
     const long long p = pidx(d, i, j, k);
-    const double V = g.compact ? (double)g.Sf[9][p] : g.V[p];
+    const double V = g.compact ? (double)g.Mf[p * kMF + MF_V] : g.V[p];
     double qq[5];
     for (int m = 0; m < 5; ++m) {
       qq[m] = q.q[m][p];

@@ -143,7 +143,7 @@ __device__ __forceinline__ void face_flux(const ConstsF& c, float La, float Lb, 
 struct Args {
   Dims d;
   ConstsF c;
-  const float* S[10];        // S^xi, S^eta, S^zeta (9), V, FP32
+  const float* M;            // FP32 metric records, kMF floats per padded node
   const double* qin[5];
   const double* qn[5];
   double* qout[5];
@@ -232,21 +232,28 @@ __device__ __forceinline__ void store_prims(const Args& A, Smem& sm, int slot, c
   }
 }
 
-// Metrics S (9) and V of this thread's halo-1 node of plane q (nb < 0: outside).
-__device__ __forceinline__ void load_metrics(const Args& A, long long nb, int q, float met[10]) {
+// Metric record of one node (three 16-byte loads).
+__device__ __forceinline__ void load_record(const float* M, long long p, float met[kMF]) {
+  const float4* r = reinterpret_cast<const float4*>(M + p * kMF);
+  const float4 a = __ldg(r), b = __ldg(r + 1), c = __ldg(r + 2);
+  met[0] = a.x; met[1] = a.y; met[2] = a.z; met[3] = a.w;
+  met[4] = b.x; met[5] = b.y; met[6] = b.z; met[7] = b.w;
+  met[8] = c.x; met[9] = c.y; met[10] = c.z; met[11] = c.w;
+}
+
+// Metric record of this thread's halo-1 node of plane q (nb < 0: outside, zeros).
+__device__ __forceinline__ void load_metrics(const Args& A, long long nb, int q, float met[kMF]) {
   if (nb < 0) {
 #pragma unroll
-    for (int f = 0; f < 10; ++f) met[f] = 0.f;
+    for (int f = 0; f < kMF; ++f) met[f] = 0.f;
     return;
   }
-  const long long p = nb + (long long)q * A.d.sk;
-#pragma unroll
-  for (int f = 0; f < 10; ++f) met[f] = __ldg(A.S[f] + p);
+  load_record(A.M, nb + (long long)q * A.d.sk, met);
 }
 
 // Nodal fluxes, spectral radii and sensors of one node of plane q (slots
 // s_m, s_0, s_p of planes q-1, q, q+1) at halo-1 index t, into ring slot g.
-__device__ void nodal(const Args& A, Smem& sm, long long nb, const float met[10], int s_m, int s_0, int s_p, int g) {
+__device__ void nodal(const Args& A, Smem& sm, long long nb, const float met[kMF], int s_m, int s_0, int s_p, int g) {
   const ConstsF& c = A.c;
   const int t = threadIdx.x;
   const int x1 = t % H1X, y1 = t / H1X;
@@ -268,8 +275,7 @@ __device__ void nodal(const Args& A, Smem& sm, long long nb, const float met[10]
   for (int dir = 0; dir < 3; ++dir)
 #pragma unroll
     for (int cc = 0; cc < 3; ++cc) S[dir][cc] = met[3 * dir + cc];
-  const float V = met[9];
-  const float iV = V > 0.f ? f_rcp(V) : 0.f;
+  const float iV = met[MF_IV];
   const float* P0 = &sm.prim[s_0][0][0];
   const float* Pm = &sm.prim[s_m][0][0];
   const float* Pp = &sm.prim[s_p][0][0];
@@ -312,7 +318,7 @@ __device__ void nodal(const Args& A, Smem& sm, long long nb, const float met[10]
   const float div = s11 + s22 + s33;
   const float SS = s11 * s11 + s22 * s22 + s33 * s33 + 2.f * (s12 * s12 + s13 * s13 + s23 * s23);
   const float Smod = f_sqrt(2.f * SS);
-  const float csd = c.C_s * cbrt_pos(V);
+  const float csd = c.C_s * met[MF_D];
   const float mu_sgs = rho * (csd * csd) * Smod;
   const float m2e = 2.f * (mu + mu_sgs);
   const float k_eff = mu * c.k_lam + mu_sgs * c.k_sgs;
@@ -457,14 +463,16 @@ __global__ void __launch_bounds__(NT, kMinBlocks) k_fused32(Args A) {
 
   for (int p = k0 - 2; p < k1; ++p) {
     // (a) metrics of plane p+1 (used in (b)); plane p+2 -> ring; prefetch plane p+3
-    float met[10];
+    float met[kMF];
     load_metrics(A, nb, p + 1, met);
     // L2 hints one plane ahead: metrics of plane p+2 (next iteration's nodal work)
     // and Q^n of plane p+1 (next iteration's update)
     if (nb >= 0 && p + 2 <= k1) {
-      const long long pm = nb + (long long)(p + 2) * d.sk;
-#pragma unroll
-      for (int f = 0; f < 10; ++f) prefetch_l2(A.S[f] + pm);
+      // a 48-byte record spans two 32-byte sectors; with the neighbours' requests every
+      // sector of the row is asked for
+      const float* pm = A.M + (nb + (long long)(p + 2) * d.sk) * kMF;
+      prefetch_l2(pm);
+      prefetch_l2(pm + 8);
     }
     if (adv && !A.rhs && p + 1 < k1) {
       const long long pq = ob + (long long)(p + 1) * d.sk;
@@ -536,10 +544,11 @@ __global__ void __launch_bounds__(NT, kMinBlocks) k_fused32(Args A) {
             const float pr = c.gm1 * (f64_to_f32(qnew[4] - c.e_inf) - 0.5f * (m1 * u + m2 * v + m3 * w)) + c.p_inf;
             const float a = f_sqrt(c.gamma * pr * ir);
             float ls = 0.f;
+            float mr[kMF];
+            load_record(A.M, pp, mr);
 #pragma unroll
             for (int dir = 0; dir < 3; ++dir) {
-              const float sx = __ldg(A.S[3 * dir] + pp), sy = __ldg(A.S[3 * dir + 1] + pp),
-                          sz = __ldg(A.S[3 * dir + 2] + pp);
+              const float sx = mr[3 * dir], sy = mr[3 * dir + 1], sz = mr[3 * dir + 2];
               ls += fabsf(sx * u + sy * v + sz * w) + a * f_sqrt(sx * sx + sy * sy + sz * sz);
             }
             rate = fmaxf(rate, ls * iV);
@@ -616,7 +625,7 @@ cudaError_t fused32_slots(int* slots) {
   return cudaSuccess;
 }
 
-cudaError_t fused32(const Dims& d, const Consts& c, float* const* Sf, const State& qin, const State& qn,
+cudaError_t fused32(const Dims& d, const Consts& c, const float* Mf, const State& qin, const State& qn,
                     const State& qout, Scalars* sc, double alpha, int want_res, int want_rate, double* rhs_flat,
                     int kchunk, cudaStream_t st) {
   const int smem = (int)sizeof(Smem);
@@ -629,7 +638,7 @@ cudaError_t fused32(const Dims& d, const Consts& c, float* const* Sf, const Stat
   A.c.kappa2 = (float)c.kappa2; A.c.kappa4 = (float)c.kappa4; A.c.p_inf = (float)c.p_inf;
   A.c.e_inf = c.p_inf / c.gm1;
   A.c.ep_inf = (float)(A.c.e_inf + c.p_inf);
-  for (int i = 0; i < 10; ++i) A.S[i] = Sf[i];
+  A.M = Mf;
   for (int m = 0; m < 5; ++m) {
     A.qin[m] = qin.q[m];
     A.qn[m] = qn.q[m];

@@ -352,7 +352,7 @@ class Grid:
         jz_compute_metrics(self.h)
 
     def compact(self):
-        """Keep FP32 metrics only (FP32-flux solvers; frees 104 bytes per padded node)."""
+        """Keep FP32 metrics only (FP32-flux solvers; frees 96 bytes per padded node)."""
         jz_grid_compact(self.h)
 
     @classmethod

@@ -75,7 +75,7 @@ def test_compact_refusals_and_memory(jz):
     grid.compact()                                   # idempotent
     free1, _ = torch.cuda.mem_get_info()
     padded = ((256 + 4 + 3) // 4 * 4) * (128 + 4) * (64 + 4)
-    assert free1 - free0 >= 0.9 * 104 * padded
+    assert free1 - free0 >= 0.9 * 96 * padded          # 144 B of FP64 arrays out, 48 B of FP32 records in
     with pytest.raises(jz.JzError, match="compact"):
         jz.Solver(grid, prm, jz.JZ_PREC_FP64)
     with pytest.raises(jz.JzError, match="compact"):
