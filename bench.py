@@ -44,9 +44,9 @@ FLOPS_PER_POINT = {"nodal": 83, "viscous": 233, "faces": 168, "update": 76}
 # dram__bytes_write.sum / nodes), scaled to the full launch by its node count;
 # profiles/k_viscous_fp64_jet256x128x64.md: (541.0 + 225.7) MB over 258 x 130 x 66 nodes.
 TRAFFIC_PER_NODE = {"viscous": 346.3}
-# k_fused32: (122.3 + 4 x 170.5) / 5 DRAM bytes per node over a step's five launches
-# (stage 1 and stage 2 captures of the current kernel in profiles/k_fused32_jet256x128x64.md).
-TRAFFIC_FUSED32_PER_NODE = (122.3 + 4 * 170.5) / 5
+# k_fused32: DRAM bytes per node averaged over a step's five launches (stage 1 and stage 2
+# captures in profiles/k_fused32_jet256x128x64.md); None until captured for the current kernel.
+TRAFFIC_FUSED32_PER_NODE = None
 
 
 def _dist():
@@ -454,7 +454,8 @@ def main():
         variants["fp32flux"] = {
             "value": v32, "unit": "Gpoint-stage/s", "ms_per_step": r32["ms"] / args.steps, "dtype": "f32 flux / f64 state",
             "roofline": {"bound": "hbm", "kernel": "fused32", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s",
-                         "frac": gbs / hbm_peak, "traffic": TRAFFIC_FUSED32_PER_NODE * npts,
+                         "frac": gbs / hbm_peak,
+                         "traffic": TRAFFIC_FUSED32_PER_NODE * npts if TRAFFIC_FUSED32_PER_NODE else None,
                          "algorithmic_bytes_per_point_stage": 152},
             "kernels": {k: {"ms_per_launch": v[0] / v[1], "launches": int(v[1]), "share": v[0] / tot32}
                         for k, v in r32["prof"].items() if v[1] > 0},
