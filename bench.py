@@ -46,7 +46,7 @@ FLOPS_PER_POINT = {"nodal": 83, "viscous": 233, "faces": 168, "update": 76}
 TRAFFIC_PER_NODE = {"viscous": 346.3}
 # k_fused32: DRAM bytes per node averaged over a step's five launches (stage 1 and stage 2
 # captures in profiles/k_fused32_jet256x128x64.md); None until captured for the current kernel.
-TRAFFIC_FUSED32_PER_NODE = None
+TRAFFIC_FUSED32_PER_NODE = (129.5 + 4 * 174.7) / 5
 
 
 def _dist():
