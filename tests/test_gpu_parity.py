@@ -220,3 +220,45 @@ def test_fp64_reciprocal_and_cube_root(jz):
     print(f"rcp64 max rel err {e_rcp:.3e}, cbrt64 max rel err {e_cbrt:.3e}")
     assert e_rcp <= 2 * 2.0 ** -52
     assert e_cbrt <= 4 * 2.0 ** -52
+
+
+@pytest.mark.parametrize("shape", [(1, 1, 1), (2, 3, 1), (3, 1, 2)])
+def test_degenerate_periodic_boxes(jz, shape):
+    """Periodic boxes one to three nodes wide (every stencil neighbour wraps onto the few
+    nodes there are): residual parity with the oracle in both forms, and a uniform flow that
+    stays exactly uniform."""
+    g = W.box_grid(*shape, h=0.3)
+    prm = W.box_params()
+    q = W.random_state(g, seed=4, amp=0.05)
+    grid = jz.Grid.from_workload(g)
+    ref = O.residual(oracle_grid(g), torch.from_numpy(q), O.Consts(prm)).numpy()
+    qu = W.random_state(g, seed=4, amp=0.0)
+    for prec, tol in ((jz.JZ_PREC_FP64, TOL_L2), (jz.JZ_PREC_FP32FLUX, 2e-4)):
+        s = jz.Solver(grid, prm, prec)
+        got = s.residual(q)
+        if np.abs(ref).max() == 0.0:
+            assert np.abs(got).max() <= 1e-14
+        else:
+            e2, _ = field_errors(got, ref)
+            assert e2.max() <= tol, (prec, e2)
+        s.set_state(qu, 0.0)
+        st = s.step(3)
+        assert np.array_equal(s.get_state(), qu) and st.t > 0.0
+        s.close()
+
+
+def test_minimal_jet_grid(jz):
+    """The smallest jet grid the ABI accepts (4 x 4 x 4): two steps against the oracle."""
+    g = W.jet_grid(4, 4, 4)
+    prm = W.jet_params(seed=2)
+    q = W.jet_state(g)
+    grid = jz.Grid.from_workload(g)
+    ref, t, _, _ = O.run(oracle_grid(g), torch.from_numpy(q), O.Consts(prm), 2)
+    for prec, tol in ((jz.JZ_PREC_FP64, TOL_L2), (jz.JZ_PREC_FP32FLUX, 1e-5)):
+        s = jz.Solver(grid, prm, prec)
+        s.set_state(q, 0.0)
+        st = s.step(2)
+        e2, _ = field_errors(s.get_state(), ref.numpy())
+        assert e2.max() <= tol, (prec, e2)
+        assert abs(st.t - t.item()) <= 1e-6 * t.item()
+        s.close()
