@@ -116,6 +116,9 @@ int jz_version(void);
  *  Returns JZ_ERR_ARG on bad sizes/pointers, JZ_ERR_OOM, JZ_ERR_CUDA. */
 int jz_create_grid(int ni, int nj, int nk, const double* xyz, const double* period,
                    int topology, jz_grid** out);
+
+/* Free the grid.  JZ_ERR_STATE (and nothing freed) while solvers created on it
+ * are alive: destroy them first. */
 int jz_destroy_grid(jz_grid* g);
 
 /* Compute the metrics of the curvilinear transformation (Algorithm 2:

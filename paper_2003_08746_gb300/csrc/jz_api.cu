@@ -456,6 +456,7 @@ int jz_create_grid(int ni, int nj, int nk, const double* xyz, const double* peri
 
 int jz_destroy_grid(jz_grid* g) {
   if (!g) return fail(JZ_ERR_ARG, "jz_destroy_grid: NULL");
+  if (g->nsolvers > 0) return fail(JZ_ERR_STATE, "jz_destroy_grid: %d solver(s) still use the grid", g->nsolvers);
   delete g;
   return JZ_OK;
 }
