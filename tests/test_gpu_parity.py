@@ -248,17 +248,23 @@ def test_degenerate_periodic_boxes(jz, shape):
 
 
 def test_minimal_jet_grid(jz):
-    """The smallest jet grid the ABI accepts (4 x 4 x 4): two steps against the oracle."""
+    """The smallest jet grid the ABI accepts (4 x 4 x 4): two steps against the oracle.  On this
+    grid only the axis line lies inside the jet, and the axis average wipes its momentum in the
+    first stage, so the momentum left is ~1e-7 of the initial scale: errors are measured
+    against the initial state's scale per field (momentum: the largest component)."""
     g = W.jet_grid(4, 4, 4)
     prm = W.jet_params(seed=2)
     q = W.jet_state(g)
+    scale = np.abs(q).reshape(5, -1).max(axis=1)
+    scale[1:4] = scale[1:4].max()
     grid = jz.Grid.from_workload(g)
     ref, t, _, _ = O.run(oracle_grid(g), torch.from_numpy(q), O.Consts(prm), 2)
-    for prec, tol in ((jz.JZ_PREC_FP64, TOL_L2), (jz.JZ_PREC_FP32FLUX, 1e-5)):
+    ref = ref.numpy()
+    for prec, tol in ((jz.JZ_PREC_FP64, 1e-13), (jz.JZ_PREC_FP32FLUX, 1e-6)):
         s = jz.Solver(grid, prm, prec)
         s.set_state(q, 0.0)
         st = s.step(2)
-        e2, _ = field_errors(s.get_state(), ref.numpy())
-        assert e2.max() <= tol, (prec, e2)
+        err = np.abs(s.get_state() - ref).reshape(5, -1).max(axis=1) / scale
+        assert err.max() <= tol, (prec, err)
         assert abs(st.t - t.item()) <= 1e-6 * t.item()
         s.close()
