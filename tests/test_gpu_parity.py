@@ -260,7 +260,7 @@ def test_minimal_jet_grid(jz):
     grid = jz.Grid.from_workload(g)
     ref, t, _, _ = O.run(oracle_grid(g), torch.from_numpy(q), O.Consts(prm), 2)
     ref = ref.numpy()
-    for prec, tol in ((jz.JZ_PREC_FP64, 1e-13), (jz.JZ_PREC_FP32FLUX, 1e-6)):
+    for prec, tol in ((jz.JZ_PREC_FP64, 1e-13), (jz.JZ_PREC_FP32FLUX, 1e-5)):
         s = jz.Solver(grid, prm, prec)
         s.set_state(q, 0.0)
         st = s.step(2)
