@@ -221,22 +221,23 @@ int mark(jz_solver* s, int kind) {
   } while (0)
 
 int run_stage64(jz_solver* s, const jz::State& in, const jz::State& out, double alpha, int want_res,
-                double* rhs_flat) {
+                double* rhs_flat, bool want_rate = false) {
   const jz::Dims& d = s->grid->d;
   const jz::GridDev& g = s->grid->g;
   JZ_RUN(JZ_PROF_NODAL, jz::nodal64(d, s->c, g, s->w, in, s->st));
   JZ_RUN(JZ_PROF_VISCOUS, jz::viscous64(d, s->c, g, s->w, in, s->st));
   JZ_RUN(JZ_PROF_FACES, jz::faces64(d, s->c, s->w, in, s->st));
-  JZ_RUN(JZ_PROF_UPDATE, jz::update64(d, g, s->w, in, s->qn, out, s->sc, alpha, want_res, rhs_flat, s->st));
+  JZ_RUN(JZ_PROF_UPDATE, jz::update64(d, g, s->w, in, s->qn, out, s->sc, alpha, want_res, rhs_flat, s->st,
+                                      want_rate ? &s->c : nullptr));
   return JZ_OK;
 }
 
 int run_step(jz_solver* s) {
   const jz::Dims& d = s->grid->d;
   const jz::GridDev& g = s->grid->g;
-  // The FP32-flux stage 5 leaves the CFL rate of Q^{n+1} behind; otherwise
-  // (FP64 form, or first step after jz_set_state) it is reduced here.
-  if (s->c.dt_fixed <= 0.0 && !(s->fp32 && s->rate_ready))
+  // Stage 5 of the previous step left the CFL rate of Q^n behind; after jz_set_state
+  // (or a fixed step) it is reduced here.
+  if (s->c.dt_fixed <= 0.0 && !s->rate_ready)
     JZ_RUN(JZ_PROF_REDUCE, jz::cfl_rate(d, s->c, g, s->qn, s->sc, s->st));
   JZ_RUN(JZ_PROF_REDUCE, jz::set_dt(s->c, s->sc, 0, s->st));
   jz::State in = s->qn;
@@ -247,7 +248,7 @@ int run_step(jz_solver* s) {
       JZ_RUN(JZ_PROF_FUSED32, jz::fused32(d, s->c, s->Mf, in, s->qn, out, s->sc, kAlpha[l], l == 0,
                                           l == 4 && s->c.dt_fixed <= 0.0, nullptr, s->kchunk, s->st));
     else
-      r = run_stage64(s, in, out, kAlpha[l], l == 0, nullptr);
+      r = run_stage64(s, in, out, kAlpha[l], l == 0, nullptr, l == 4 && s->c.dt_fixed <= 0.0);
     if (r) return r;
     if (d.topo == JZ_TOPO_JET) {
       JZ_RUN(JZ_PROF_BC, jz::bc_farfield(d, s->c, g, out, s->st));
@@ -263,7 +264,7 @@ int run_step(jz_solver* s) {
   s->qa = t;
   JZ_RUN(JZ_PROF_REDUCE, jz::set_dt(s->c, s->sc, 1, s->st));
   s->steps += 1;
-  s->rate_ready = s->fp32 && s->c.dt_fixed <= 0.0;
+  s->rate_ready = s->c.dt_fixed <= 0.0;
   return JZ_OK;
 }
 
@@ -272,12 +273,12 @@ int run_step(jz_solver* s) {
 // roles of the Q^n and stage buffers swap every step and come back after two; so two steps
 // are captured once per starting buffer (on a private stream, nothing executes while
 // capturing) and replayed with one launch.  Not used while profiling (events between
-// kernels), while flow statistics are sampled, or before the FP32-flux form has a CFL rate.
+// kernels), while flow statistics are sampled, or before the first step has left a CFL rate.
 // Any capture failure turns graphs off for the solver; the steps then run as plain launches.
 int graph_two_steps(jz_solver* s, bool* done) {
   *done = false;
   if (s->graphs_off || s->prof || s->fs_every > 0) return JZ_OK;
-  if (s->fp32 && s->c.dt_fixed <= 0.0 && !s->rate_ready) return JZ_OK;
+  if (s->c.dt_fixed <= 0.0 && !s->rate_ready) return JZ_OK;
   int slot = s->gkey[0] == s->qn.q[0] ? 0 : (s->gkey[1] == s->qn.q[0] ? 1 : -1);
   if (slot < 0) {
     slot = s->gexec[0] ? 1 : 0;
@@ -326,7 +327,7 @@ int graph_two_steps(jz_solver* s, bool* done) {
   JZ_CK(cudaGraphLaunch(s->gexec[slot], s->st));
   for (int k = 0; k < JZ_NPROF; ++k) s->launches[k] += s->glaunch[slot][k];
   s->steps += 2;
-  s->rate_ready = s->fp32 && s->c.dt_fixed <= 0.0;
+  s->rate_ready = s->c.dt_fixed <= 0.0;
   *done = true;
   return JZ_OK;
 }
@@ -759,6 +760,7 @@ int jz_adjoint_step(jz_solver* s, const double* forcing_amps, int nsteps, int ck
   if (!s || !forcing_amps || !J_out || !grad_out) return fail(JZ_ERR_ARG, "jz_adjoint_step: NULL argument");
   if (nsteps < 1 || ckpt_every < 1) return fail(JZ_ERR_ARG, "jz_adjoint_step: nsteps and ckpt_every must be >= 1");
   if (s->fp32) return fail(JZ_ERR_ARG, "jz_adjoint_step: the adjoint is available for the FP64 form");
+  s->rate_ready = false;     // the sweep below reduces its own (frozen) rate into the scalars
   const jz::Dims& d = s->grid->d;
   const jz::GridDev& g = s->grid->g;
   if (d.topo != JZ_TOPO_JET) return fail(JZ_ERR_ARG, "jz_adjoint_step: the observer functional needs a jet grid");

@@ -150,6 +150,34 @@ struct Scalars {
   int pad_;
 };
 
+// CFL rate of one node, (lambda_xi + lambda_eta + lambda_zeta) / V with
+// lambda_d = |S^d . u| + a |S^d|, from its conserved variables.  Shared by the
+// stand-alone reduction and the stage-5 update so that both give the same bits.
+__device__ __forceinline__ double node_rate(const GridDev& g, const Consts& c, long long p, double rho, double m1,
+                                            double m2, double m3, double e) {
+  const double ir = rcp64(rho);
+  const double u = m1 * ir, v = m2 * ir, w = m3 * ir;
+  const double pr = c.gm1 * (e - 0.5 * (m1 * u + m2 * v + m3 * w));
+  const double a = sqrt(c.gamma * pr * ir);
+  double lsum = 0.0;
+  if (!g.compact) {
+    for (int dir = 0; dir < 3; ++dir) {
+      const double U = g.S[3 * dir][p] * u + g.S[3 * dir + 1][p] * v + g.S[3 * dir + 2][p] * w;
+      const double lam = fabs(U) + a * g.Smag[dir][p];
+      lsum = dir == 0 ? lam : lsum + lam;
+    }
+    return lsum * g.invV[p];
+  }
+  // compact grid: the same rate from the FP32 metrics, widened
+  const float* M = g.Mf + p * kMF;
+  for (int dir = 0; dir < 3; ++dir) {
+    const double sx = M[3 * dir], sy = M[3 * dir + 1], sz = M[3 * dir + 2];
+    const double lam = fabs(sx * u + sy * v + sz * w) + a * sqrt(sx * sx + sy * sy + sz * sz);
+    lsum = dir == 0 ? lam : lsum + lam;
+  }
+  return lsum * (double)M[MF_IV];
+}
+
 // FP64 stage scratch arrays (each Np elements).
 struct Work64 {
   double* u; double* v; double* w; double* T; double* p; double* mu;
@@ -217,7 +245,8 @@ cudaError_t faces64(const Dims& d, const Consts& c, const Work64& w, const State
 // stage update (rhs_flat == nullptr) or RHS output to rhs_flat [5][N]
 cudaError_t update64(const Dims& d, const GridDev& g, const Work64& w, const State& qin, const State& qn,
                      const State& qout, const Scalars* sc, double alpha, int want_res, double* rhs_flat,
-                     cudaStream_t st);
+                     cudaStream_t st,
+                     const Consts* rate_consts = nullptr);
 // FP32-flux stage (one fused kernel); Mf = the FP32 metric records (kMF floats per padded node).
 cudaError_t fused32(const Dims& d, const Consts& c, const float* Mf, const State& qin, const State& qn,
                     const State& qout, Scalars* sc, double alpha, int want_res, int want_rate, double* rhs_flat,

@@ -21,29 +21,7 @@ __global__ void k_cfl_rate(Dims d, GridDev g, State q, Consts c, Scalars* sc) {
   if (box_coord(b, blockIdx.x * (long long)blockDim.x + threadIdx.x, i, j, k) &&
       (d.topo != JZ_TOPO_JET || (i >= 1 && i <= d.ni - 2 && j >= 1 && j <= d.nj - 2))) {
     const long long p = pidx(d, i, j, k);
-    const double rho = q.q[0][p], m1 = q.q[1][p], m2 = q.q[2][p], m3 = q.q[3][p];
-    const double ir = rcp64(rho);
-    const double u = m1 * ir, v = m2 * ir, w = m3 * ir;
-    const double pr = c.gm1 * (q.q[4][p] - 0.5 * (m1 * u + m2 * v + m3 * w));
-    const double a = sqrt(c.gamma * pr * ir);
-    double lsum = 0.0;
-    if (!g.compact) {
-      for (int dir = 0; dir < 3; ++dir) {
-        const double U = g.S[3 * dir][p] * u + g.S[3 * dir + 1][p] * v + g.S[3 * dir + 2][p] * w;
-        const double lam = fabs(U) + a * g.Smag[dir][p];
-        lsum = dir == 0 ? lam : lsum + lam;
-      }
-      rate = lsum * g.invV[p];
-    } else {
-      // compact grid: the same rate from the FP32 metrics, widened
-      const float* M = g.Mf + p * kMF;
-      for (int dir = 0; dir < 3; ++dir) {
-        const double sx = M[3 * dir], sy = M[3 * dir + 1], sz = M[3 * dir + 2];
-        const double lam = fabs(sx * u + sy * v + sz * w) + a * sqrt(sx * sx + sy * sy + sz * sz);
-        lsum = dir == 0 ? lam : lsum + lam;
-      }
-      rate = lsum * (double)M[MF_IV];
-    }
+    rate = node_rate(g, c, p, q.q[0][p], q.q[1][p], q.q[2][p], q.q[3][p], q.q[4][p]);
   }
   __shared__ double red[kTPB / 32];
   rate = warp_max(rate);

@@ -164,14 +164,18 @@ __global__ void __launch_bounds__(kTPB) k_faces(Dims d, Consts c, Work64 w, Stat
 }
 
 // mode 0: stage update; mode 1: write RHS to rhs_flat (unpadded [5][N]).
+// want_rate (stage 5): also the CFL rate of the new state at the advanced nodes, reduced
+// into rate_max for the next step (the boundary conditions applied afterwards touch no
+// advanced node), with the same arithmetic as the stand-alone reduction.
 template <int MODE>
 __global__ void __launch_bounds__(kTPB) k_update(Dims d, GridDev g, Work64 w, State qin, State qn, State qout,
                                                  const Scalars* sc, double alpha, int want_res,
-                                                 double* rhs_flat, double* res_sum) {
+                                                 double* rhs_flat, double* res_sum, Consts c, int want_rate,
+                                                 double* rate_max) {
   Box b{0, 0, 0, d.ni, d.nj, d.nk};
   int i, j, k;
   const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  double r2 = 0.0;
+  double r2 = 0.0, rate = 0.0;
   if (box_coord(b, t, i, j, k)) {
     const long long p = pidx(d, i, j, k);
     const long long s[3] = {1, d.sj, d.sk};
@@ -195,7 +199,12 @@ __global__ void __launch_bounds__(kTPB) k_update(Dims d, GridDev g, Work64 w, St
     }
     if (MODE == 0) {
       const double adt = alpha * sc->dt;
-      for (int m = 0; m < 5; ++m) qout.q[m][p] = adv ? qn.q[m][p] - adt * R[m] : qin.q[m][p];
+      double qnew[5];
+      for (int m = 0; m < 5; ++m) {
+        qnew[m] = adv ? qn.q[m][p] - adt * R[m] : qin.q[m][p];
+        qout.q[m][p] = qnew[m];
+      }
+      if (want_rate && adv) rate = node_rate(g, c, p, qnew[0], qnew[1], qnew[2], qnew[3], qnew[4]);
     } else {
       const long long N = (long long)d.ni * d.nj * d.nk;
       for (int m = 0; m < 5; ++m) rhs_flat[m * N + t] = adv ? R[m] : 0.0;
@@ -212,6 +221,20 @@ __global__ void __launch_bounds__(kTPB) k_update(Dims d, GridDev g, Work64 w, St
       double x = threadIdx.x < kTPB / 32 ? red[threadIdx.x] : 0.0;
       for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
       if (threadIdx.x == 0) atomicAdd(res_sum, x);
+    }
+  }
+  if (MODE == 0 && want_rate) {
+    // block max -> one atomic per block (non-negative doubles order like their bits)
+    __shared__ double redm[kTPB / 32];
+    for (int o = 16; o > 0; o >>= 1) rate = fmax(rate, __shfl_xor_sync(0xffffffffu, rate, o));
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) redm[threadIdx.x >> 5] = rate;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+      double x = threadIdx.x < kTPB / 32 ? redm[threadIdx.x] : 0.0;
+      for (int o = 16; o > 0; o >>= 1) x = fmax(x, __shfl_xor_sync(0xffffffffu, x, o));
+      if (threadIdx.x == 0 && x > 0.0)
+        atomicMax(reinterpret_cast<unsigned long long*>(rate_max), (unsigned long long)__double_as_longlong(x));
     }
   }
 }
@@ -240,14 +263,18 @@ cudaError_t faces64(const Dims& d, const Consts& c, const Work64& w, const State
 
 cudaError_t update64(const Dims& d, const GridDev& g, const Work64& w, const State& qin, const State& qn,
                      const State& qout, const Scalars* sc, double alpha, int want_res, double* rhs_flat,
-                     cudaStream_t st) {
+                     cudaStream_t st, const Consts* rate_consts) {
   const long long nr = (long long)d.ni * d.nj * d.nk;
   double* res_sum = const_cast<double*>(&sc->res_sum);
+  double* rate_max = const_cast<double*>(&sc->rate_max);
+  const Consts c = rate_consts ? *rate_consts : Consts{};
+  const int want_rate = rate_consts && !rhs_flat ? 1 : 0;
   if (rhs_flat)
-    k_update<1><<<blocks_for(nr, kTPB), kTPB, 0, st>>>(d, g, w, qin, qn, qout, sc, alpha, 0, rhs_flat, res_sum);
+    k_update<1><<<blocks_for(nr, kTPB), kTPB, 0, st>>>(d, g, w, qin, qn, qout, sc, alpha, 0, rhs_flat, res_sum, c,
+                                                       0, rate_max);
   else
     k_update<0><<<blocks_for(nr, kTPB), kTPB, 0, st>>>(d, g, w, qin, qn, qout, sc, alpha, want_res, nullptr,
-                                                       res_sum);
+                                                       res_sum, c, want_rate, rate_max);
   return cudaGetLastError();
 }
 
