@@ -572,8 +572,10 @@ int jz_create(jz_grid* g, const jz_params* p, void* stream, jz_solver** out) {
       own_mf = reinterpret_cast<float*>(tmp);
       s->Mf = own_mf;
     }
-    // CTAs of 30 x 8 columns marching in k.  Split k into chunks so that the CTA count fills
-    // the resident slots evenly: minimise (waves) x (planes per CTA + the 3 priming planes).
+    // CTAs of 30 x 8 columns marching in k.  Split k into chunks of at least 16 planes so that
+    // there are about ten waves of CTAs or more over the resident slots (measured: fewer,
+    // longer CTAs balance worse), and among those pick the count that minimises
+    // (waves) x (planes per CTA + the 3 priming planes).
     const int tx = jz::fused32_tile_x(), ty = jz::fused32_tile_y();
     const long long tiles = (long long)((d.ni + tx - 1) / tx) * ((d.nj + ty - 1) / ty);
     int slots = 304;
@@ -581,9 +583,11 @@ int jz_create(jz_grid* g, const jz_params* p, void* stream, jz_solver** out) {
       cudaGetLastError();
       slots = 304;
     }
-    int best = 1;
+    const int nmax = std::max(1, d.nk / 16);
+    const int nmin = (int)std::min<long long>(nmax, (10LL * slots + tiles - 1) / tiles);
+    int best = nmin;
     long long best_cost = -1;
-    for (int nch = 1; nch <= std::max(1, d.nk / 8); ++nch) {
+    for (int nch = nmin; nch <= nmax; ++nch) {
       const long long waves = (tiles * nch + slots - 1) / slots;
       const long long cost = waves * ((d.nk + nch - 1) / nch + 3);
       if (best_cost < 0 || cost < best_cost) {
