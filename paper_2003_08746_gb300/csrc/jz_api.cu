@@ -368,6 +368,20 @@ int fwd_step(jz_solver* s, const jz::State& in, const jz::State& out, double t, 
   return JZ_OK;
 }
 
+// One time step in -> out that leaves the four intermediate stage states in keep[0..3].
+int fwd_step_keep(jz_solver* s, const jz::State& in, const jz::State& out, double t, double dt,
+                  const jz::State keep[4]) {
+  JZ_CK(jz::set_time(s->sc, t, dt, s->st));
+  const jz::State* src = &in;
+  for (int l = 0; l < 5; ++l) {
+    const jz::State& dst = l == 4 ? out : keep[l];
+    int r = fwd_stage(s, *src, in, dst, l);
+    if (r) return r;
+    src = &dst;
+  }
+  return JZ_OK;
+}
+
 int copy_state(jz_solver* s, const jz::State& dst, const jz::State& src) {
   const size_t bytes = sizeof(double) * s->grid->d.Np;
   for (int m = 0; m < 5; ++m) JZ_CK(cudaMemcpyAsync(dst.q[m], src.q[m], bytes, cudaMemcpyDeviceToDevice, s->st));
@@ -828,6 +842,25 @@ int jz_adjoint_step(jz_solver* s, const double* forcing_amps, int nsteps, int ck
   for (auto& st : stg) AS(st);
   AS(wa); AS(wb);
   if (e != cudaSuccess) return fail(alloc_status(e), "jz_adjoint_step: device allocation failed: %s", cudaGetErrorString(e));
+  // Where memory allows, the segment recompute keeps the four intermediate stage states of
+  // every step, so that the reverse sweep does not recompute them step by step (one forward
+  // step per step less).  Kept only if they take under half of the free device memory.
+  std::vector<jz::State> kept;
+  {
+    size_t free_b = 0, total_b = 0;
+    const size_t need = (size_t)C * 4 * 5 * sizeof(double) * (size_t)d.Np;
+    if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess && need < free_b / 2) {
+      kept.resize((size_t)C * 4);
+      for (auto& st : kept) AS(st);
+      if (e != cudaSuccess) {        // not enough after all: run without them
+        cudaGetLastError();
+        e = cudaSuccess;
+        kept.clear();
+      }
+    } else {
+      cudaGetLastError();
+    }
+  }
   JZ_CK(cudaMemcpyAsync(wdev, w.data(), sizeof(double) * d.ni, cudaMemcpyHostToDevice, s->st));
   // frozen time step and start time
   if (s->c.dt_fixed <= 0.0) JZ_RUN(JZ_PROF_REDUCE, jz::cfl_rate(d, s->c, g, s->qn, s->sc, s->st));
@@ -868,7 +901,8 @@ int jz_adjoint_step(jz_solver* s, const double* forcing_amps, int nsteps, int ck
     r = copy_state(s, seg[0], ck[sg]);
     if (r) return r;
     for (int q = 0; q < n1 - n0; ++q) {
-      r = fwd_step(s, seg[q], seg[q + 1], t0 + (n0 + q) * dt, dt);
+      r = kept.empty() ? fwd_step(s, seg[q], seg[q + 1], t0 + (n0 + q) * dt, dt)
+                       : fwd_step_keep(s, seg[q], seg[q + 1], t0 + (n0 + q) * dt, dt, &kept[(size_t)q * 4]);
       if (r) return r;
     }
     for (int n = n1 - 1; n >= n0; --n) {
@@ -876,12 +910,15 @@ int jz_adjoint_step(jz_solver* s, const double* forcing_amps, int nsteps, int ck
       const jz::State& Qn1 = seg[n - n0 + 1];
       const double tn = t0 + n * dt;
       JZ_RUN(JZ_PROF_ADJOINT, jz::observer(d, s->c, Qn1, wdev, j0, beta, dt, a, 1, s->st));
-      // stage states of step n
-      JZ_CK(jz::set_time(s->sc, tn, dt, s->st));
-      const jz::State* st[6] = {&Qn, &stg[0], &stg[1], &stg[2], &stg[3], &Qn1};
-      for (int l = 0; l < 4; ++l) {
-        r = fwd_stage(s, *st[l], Qn, *st[l + 1], l);
-        if (r) return r;
+      // stage states of step n: kept by the segment recompute, or recomputed here
+      const jz::State* sv = kept.empty() ? stg.data() : &kept[(size_t)(n - n0) * 4];
+      const jz::State* st[6] = {&Qn, &sv[0], &sv[1], &sv[2], &sv[3], &Qn1};
+      if (kept.empty()) {
+        JZ_CK(jz::set_time(s->sc, tn, dt, s->st));
+        for (int l = 0; l < 4; ++l) {
+          r = fwd_stage(s, *st[l], Qn, *st[l + 1], l);
+          if (r) return r;
+        }
       }
       for (int l = 4; l >= 0; --l) {
         JZ_RUN(JZ_PROF_ADJOINT, jz::adj_bcs(d, s->c, g, s->in, *st[l + 1], a, tn + kAlpha[l] * dt, s->st));
