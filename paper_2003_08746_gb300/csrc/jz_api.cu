@@ -586,10 +586,11 @@ int jz_create(jz_grid* g, const jz_params* p, void* stream, jz_solver** out) {
       own_mf = reinterpret_cast<float*>(tmp);
       s->Mf = own_mf;
     }
-    // CTAs of 30 x 8 columns marching in k.  Split k into chunks of at least 16 planes so that
-    // there are about ten waves of CTAs or more over the resident slots (measured: fewer,
-    // longer CTAs balance worse), and among those pick the count that minimises
-    // (waves) x (planes per CTA + the 3 priming planes).
+    // CTAs of 30 x 8 columns marching in k, the k range split into chunks.  Rule fitted to
+    // chunk-count sweeps over eight workloads (box 32x24x16 to jet 1000x400x500): about 32
+    // planes per CTA, but at least two waves of CTAs over the resident slots (small grids are
+    // latency-bound: more, shorter CTAs win even with the 3 priming planes each) and at most
+    // thirty (large grids: longer CTAs amortise the priming).
     const int tx = jz::fused32_tile_x(), ty = jz::fused32_tile_y();
     const long long tiles = (long long)((d.ni + tx - 1) / tx) * ((d.nj + ty - 1) / ty);
     int slots = 304;
@@ -597,18 +598,9 @@ int jz_create(jz_grid* g, const jz_params* p, void* stream, jz_solver** out) {
       cudaGetLastError();
       slots = 304;
     }
-    const int nmax = std::max(1, d.nk / 16);
-    const int nmin = (int)std::min<long long>(nmax, (10LL * slots + tiles - 1) / tiles);
-    int best = nmin;
-    long long best_cost = -1;
-    for (int nch = nmin; nch <= nmax; ++nch) {
-      const long long waves = (tiles * nch + slots - 1) / slots;
-      const long long cost = waves * ((d.nk + nch - 1) / nch + 3);
-      if (best_cost < 0 || cost < best_cost) {
-        best_cost = cost;
-        best = nch;
-      }
-    }
+    long long best = std::max(1, (d.nk + 16) / 32);
+    if (tiles * best < 2LL * slots) best = std::min<long long>(d.nk, (2LL * slots + tiles - 1) / tiles);
+    if (tiles * best > 30LL * slots) best = std::max<long long>(1, 30LL * slots / tiles);
     s->kchunk = (d.nk + best - 1) / best;
   } else {
     A(s->w.u, d.Np); A(s->w.v, d.Np); A(s->w.w, d.Np); A(s->w.T, d.Np); A(s->w.p, d.Np); A(s->w.mu, d.Np);
