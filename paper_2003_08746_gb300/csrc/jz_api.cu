@@ -854,6 +854,16 @@ int jz_adjoint_step(jz_solver* s, const double* forcing_amps, int nsteps, int ck
     }
   }
   JZ_CK(cudaMemcpyAsync(wdev, w.data(), sizeof(double) * d.ni, cudaMemcpyHostToDevice, s->st));
+  // the solver's own time and last step are left as they were (the sweeps below set the
+  // time of every step they recompute)
+  jz::Scalars h0;
+  JZ_CK(cudaMemcpyAsync(&h0, s->sc, sizeof h0, cudaMemcpyDeviceToHost, s->st));
+  JZ_CK(cudaStreamSynchronize(s->st));
+  struct RestoreTime {
+    jz_solver* s;
+    double t, dt;
+    ~RestoreTime() { jz::set_time(s->sc, t, dt, s->st); }
+  } restore_time{s, h0.t, h0.dt};
   // frozen time step and start time
   if (s->c.dt_fixed <= 0.0) JZ_RUN(JZ_PROF_REDUCE, jz::cfl_rate(d, s->c, g, s->qn, s->sc, s->st));
   JZ_RUN(JZ_PROF_REDUCE, jz::set_dt(s->c, s->sc, 0, s->st));

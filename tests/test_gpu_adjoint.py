@@ -114,3 +114,22 @@ def test_jet_functional_autograd(jz):
     J.backward()
     _, gr = jz.jz_adjoint_step(s.h, A.detach().numpy(), 4, 2, 0.75)
     assert torch.allclose(A.grad, torch.from_numpy(gr), rtol=0, atol=1e-15 * np.abs(gr).max() + 1e-300)
+
+
+def test_adjoint_leaves_solver_time_and_state(jz):
+    """jz_adjoint_step does not advance the solver: its time, step count and state are the
+    same afterwards, and a time step after it matches one without it."""
+    g, prm, q, grid, s = _setup(jz, (24, 16, 8))
+    s.step(2)
+    before = s.step(0)
+    q_before = s.get_state()
+    A = np.asarray(prm.forcing_amp)
+    jz.jz_adjoint_step(s.h, A, 5, 2, 0.75)
+    after = s.step(0)
+    assert after.t == before.t and after.steps == before.steps
+    assert np.array_equal(s.get_state(), q_before)
+    ref = jz.Solver(grid, prm)
+    ref.set_state(q, 0.0)
+    ref.step(2)
+    a, b = s.step(3), ref.step(3)
+    assert a.t == b.t and np.array_equal(s.get_state(), ref.get_state())
