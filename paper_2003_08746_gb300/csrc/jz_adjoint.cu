@@ -213,38 +213,34 @@ __global__ void k_adj_nodal(Dims d, Consts c, GridDev g, Work64 w, State q, Adj6
   int i, j, k;
   if (!box_coord(b, blockIdx.x * (long long)blockDim.x + threadIdx.x, i, j, k)) return;
   const long long p = pidx(d, i, j, k);
-  // gathers: a real node's neighbours up to two away all lie in the padded box, so they are
-  // read by offset; ghost nodes check every neighbour (0 outside the box)
-  const bool inner = i >= 0 && i < d.ni && j >= 0 && j < d.nj && k >= 0 && k < d.nk;
-  auto ld = [=](const double* f, int dir, int off) -> double {
-    const long long sd = dir == 0 ? 1 : (dir == 1 ? d.sj : d.sk);
-    return inner ? f[p + off * sd] : nb(d, f, i, j, k, dir, off);
-  };
+  // gathers
   double fb[4];
   for (int n = 0; n < 4; ++n) {
-    double v = n < 3 ? a.ubd[n][p] : 0.0;
-    for (int dir = 0; dir < 3; ++dir) v += 0.5 * (ld(a.G[n][dir], dir, -1) - ld(a.G[n][dir], dir, 1));
+    double v = n < 3 ? nb(d, a.ubd[n], i, j, k, 0, 0) : 0.0;
+    for (int dir = 0; dir < 3; ++dir)
+      v += 0.5 * (nb(d, a.G[n][dir], i, j, k, dir, -1) - nb(d, a.G[n][dir], i, j, k, dir, 1));
     fb[n] = v;
   }
   double pb = 0.0;
-  for (int dir = 0; dir < 3; ++dir) pb += a.c0[dir][p] + ld(a.cpm[dir], dir, -1) + ld(a.cpm[dir], dir, 1);
+  for (int dir = 0; dir < 3; ++dir)
+    pb += nb(d, a.c0[dir], i, j, k, 0, 0) + nb(d, a.cpm[dir], i, j, k, dir, -1) + nb(d, a.cpm[dir], i, j, k, dir, 1);
   double Eb[3][5], Lamb[3];
-#pragma unroll
   for (int dir = 0; dir < 3; ++dir) {
-#pragma unroll
-    for (int m = 0; m < 5; ++m) Eb[dir][m] = 0.5 * (ld(a.acc[m], dir, -1) - ld(a.acc[m], dir, 1));
-    Lamb[dir] = a.lfh[dir][p] + ld(a.lfh[dir], dir, -1);
+    for (int m = 0; m < 5; ++m)
+      Eb[dir][m] = 0.5 * (nb(d, a.acc[m], i, j, k, dir, -1) - nb(d, a.acc[m], i, j, k, dir, 1));
+    Lamb[dir] = nb(d, a.lfh[dir], i, j, k, 0, 0) + nb(d, a.lfh[dir], i, j, k, dir, -1);
   }
   double qb[5];
   for (int m = 0; m < 5; ++m) {
     double v = 0.0;
     for (int dir = 0; dir < 3; ++dir)
-      v += ld(a.d3b[dir][m], dir, -2) + ld(a.d1b[dir][m], dir, -1) - 3.0 * ld(a.d3b[dir][m], dir, -1) -
-           a.d1b[dir][m][p] + 3.0 * a.d3b[dir][m][p] - ld(a.d3b[dir][m], dir, 1);
+      v += nb(d, a.d3b[dir][m], i, j, k, dir, -2) + nb(d, a.d1b[dir][m], i, j, k, dir, -1) -
+           3.0 * nb(d, a.d3b[dir][m], i, j, k, dir, -1) - nb(d, a.d1b[dir][m], i, j, k, 0, 0) +
+           3.0 * nb(d, a.d3b[dir][m], i, j, k, 0, 0) - nb(d, a.d3b[dir][m], i, j, k, dir, 1);
     qb[m] = v;
   }
-  qb[0] += a.rhob[p];
-  double mub = a.mub[p];
+  qb[0] += nb(d, a.rhob, i, j, k, 0, 0);
+  double mub = nb(d, a.mub, i, j, k, 0, 0);
   // forward nodal quantities
   double Q[5];
   load5(q, p, Q);
