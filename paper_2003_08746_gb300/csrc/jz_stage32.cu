@@ -155,10 +155,10 @@ struct Args {
   int want_rate;
 };
 
-// Halo-2 point loaded by this thread in round r: round 0 covers points 0..NT-1;
-// round 1 goes first to the threads that have no output node (the warps past
-// the output rows, then the unused lanes of the output warps), then to the
-// lowest threads.  -1: none.
+// Halo-2 point loaded by this thread in load pass r: pass r = 0 covers points 0..NT-1;
+// the remaining points (pass r = 1) go first to the threads that have no output node
+// (the warps past the output rows, then the unused lanes of the output warps), then to
+// the lowest threads.  -1: none.
 __device__ __forceinline__ int load_point(int r) {
   const int t = threadIdx.x;
   if (r == 0) return t < NP2 ? t : -1;
