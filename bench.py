@@ -39,7 +39,10 @@ FP64_PEAK_TFLOPS = 152 * 4 * 2.07e9 / 1e12
 # Algorithmic FP64 flops per point of each FP64 stage kernel (add/sub/mul = 1,
 # fused multiply-add = 2, divide/sqrt/cbrt = 1), counted from the operations
 # the method needs per node (each quantity once).
-FLOPS_PER_POINT = {"nodal": 83, "viscous": 233, "faces": 168, "update": 76}
+# Viscous: 12 differences, 12 metric contractions (60), strain and |S| terms (21), SGS and
+# transport coefficients (12), stresses (9), work + heat flux (21), H^d -= S^d.F (72),
+# sensors (21) = 227.
+FLOPS_PER_POINT = {"nodal": 83, "viscous": 227, "faces": 168, "update": 76}
 # DRAM bytes per node of a kernel launch from an ncu capture (dram__bytes_read.sum +
 # dram__bytes_write.sum / nodes), scaled to the full launch by its node count;
 # profiles/k_viscous_fp64_jet256x128x64.md: (541.0 + 225.7) MB over 258 x 130 x 66 nodes.

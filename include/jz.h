@@ -273,14 +273,16 @@ int jz_potential_core(const double* axis, const double* x, int ni, double u_jet,
 
 /* ---- arithmetic self-check -------------------------------------------------- *
  * The FP64 form computes reciprocals (1/rho, the Sutherland and pressure-sensor
- * denominators) and the cube roots of the anisotropic spectral-radius scaling
- * with the library's own routines: a hardware reciprocal seed refined by two
- * Newton-Raphson steps, and an FP32 seed of x^(1/3) refined by one Halley step.
- * jz_check_math runs both on 2^20 arguments spread over [1e-30, 1e30] on the
- * current device and returns the largest relative error against IEEE division
- * (1.0/x) and the CUDA math library's cbrt.  No counterpart in the paper.
+ * denominators), square roots (sound speed, strain-rate magnitude) and the
+ * powers x^(1/3), x^(2/3) of the anisotropic spectral-radius scaling with the
+ * library's own routines: a hardware seed (reciprocal) or an FP32 seed (inverse
+ * square and cube root) refined by one third-order Householder step.
+ * jz_check_math runs them on 2^20 arguments spread over [1e-30, 1e30] (and 0) on
+ * the current device and returns the largest relative error against IEEE
+ * division (1.0/x), the CUDA math library's cbrt (x^(1/3) and cbrt(x*x)) and
+ * IEEE sqrt.  No counterpart in the paper.
  * Synchronous (legacy default stream).  Errors: JZ_ERR_ARG (NULL), JZ_ERR_CUDA. */
-int jz_check_math(double* rcp_max_rel, double* cbrt_max_rel);
+int jz_check_math(double* rcp_max_rel, double* cbrt_max_rel, double* sqrt_max_rel);
 
 /* ---- snapshots (checkpoint / restart) ------------------------------------ *
  * The paper restarts long runs from stored solution files (Algorithm 2

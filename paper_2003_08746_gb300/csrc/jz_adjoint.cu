@@ -141,7 +141,7 @@ __global__ void k_adj_visc(Dims d, Consts c, GridDev g, Work64 w, State q, Adj64
   double SS = 0.0;
   for (int x = 0; x < 3; ++x)
     for (int y = 0; y < 3; ++y) SS = SS + Sij[x][y] * Sij[x][y];
-  const double Smod = sqrt(2.0 * SS);
+  const double Smod = sqrt64(2.0 * SS);
   const double mu = w.mu[p];
   const double csd = c.C_s * g.Delta[p];
   const double rho = q.q[0][p];
@@ -252,7 +252,7 @@ __global__ void __launch_bounds__(kTPBN, 3) k_adj_nodal(Dims d, Consts c, GridDe
   const double u[3] = {Q[1] * ir, Q[2] * ir, Q[3] * ir};
   const double pr = c.gm1 * (Q[4] - 0.5 * (Q[1] * u[0] + Q[2] * u[1] + Q[3] * u[2]));
   const double T = c.gamma * pr * ir;
-  const double aa = sqrt(T);
+  const double aa = sqrt64(T);
   const double iTS = rcp64(T + c.S_hat);
   const double mu = c.mu_ref * (T * aa) * c.sut_num * iTS;
   double Sv[3][3], Smag[3], U[3], lam[3];
@@ -268,10 +268,11 @@ __global__ void __launch_bounds__(kTPBN, 3) k_adj_nodal(Dims d, Consts c, GridDe
     double lo[3], hi[3], dlo[3], dhi[3];
     for (int dd = 0; dd < 3; ++dd) {
       if (c.sigma_is_two_thirds) {
-        const double t = cbrt64(lam[dd]);
+        double t, t2;
+        cbrt_pair64(lam[dd], t, t2);                        // lam^(1/3), lam^(2/3)
         lo[dd] = t;
-        hi[dd] = t * t;
-        dlo[dd] = t != 0.0 ? rcp64(3.0 * t * t) : 0.0;      // d t / d lam
+        hi[dd] = t2;
+        dlo[dd] = t != 0.0 ? rcp64(3.0 * t2) : 0.0;         // d t / d lam
         dhi[dd] = 2.0 * t * dlo[dd];                        // d t^2 / d lam
       } else {
         const bool pos = lam[dd] > 0.0;

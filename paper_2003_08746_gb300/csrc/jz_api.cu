@@ -1179,17 +1179,18 @@ int jz_stats_end(jz_solver* s) {
   return JZ_OK;
 }
 
-int jz_check_math(double* rcp_max_rel, double* cbrt_max_rel) {
-  if (!rcp_max_rel || !cbrt_max_rel) return fail(JZ_ERR_ARG, "jz_check_math: NULL argument");
+int jz_check_math(double* rcp_max_rel, double* cbrt_max_rel, double* sqrt_max_rel) {
+  if (!rcp_max_rel || !cbrt_max_rel || !sqrt_max_rel) return fail(JZ_ERR_ARG, "jz_check_math: NULL argument");
   double* dev = nullptr;
-  JZ_CK(cudaMalloc(&dev, 2 * sizeof(double)));
-  double h[2] = {0.0, 0.0};
+  JZ_CK(cudaMalloc(&dev, 3 * sizeof(double)));
+  double h[3] = {0.0, 0.0, 0.0};
   cudaError_t e = jz::math_check(dev, nullptr);
   if (e == cudaSuccess) e = cudaMemcpy(h, dev, sizeof h, cudaMemcpyDeviceToHost);
   cudaFree(dev);
   if (e != cudaSuccess) return fail(JZ_ERR_CUDA, "jz_check_math: %s", cudaGetErrorString(e));
   *rcp_max_rel = h[0];
   *cbrt_max_rel = h[1];
+  *sqrt_max_rel = h[2];
   return JZ_OK;
 }
 

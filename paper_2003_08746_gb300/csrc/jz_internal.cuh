@@ -41,42 +41,84 @@ inline Dims make_dims(int ni, int nj, int nk, int topo) {
   return d;
 }
 
-// FP64 reciprocal and cube root with fewer FP64-pipe instructions than IEEE
-// division and the library cube root; the FP64 form is bound by that pipe.
-// Both are accurate to about one unit in the last place (checked against
-// 1.0/x and cbrt(x) by jz_check_math), far inside the form's 1e-12 parity.
+// FP64 reciprocal, square root and cube root with fewer FP64-pipe instructions
+// than IEEE division and the library routines; the FP64 form is bound by that
+// pipe (about 1/64 of an SM sub-partition's issue rate), while integer and
+// FP32 work issues almost for free beside it.  All three are accurate to about
+// one unit in the last place (checked against 1.0/x, sqrt(x) and cbrt(x) by
+// jz_check_math), far inside the form's 1e-12 parity.
+//
+// The refinements are the third-order (Householder) iterations for a root:
+// with a seed y of r = x^(1/n) or of 1/r and the residual e = 1 - (seed
+// relation), the exact correction factor (1 - e)^(-1/n) is expanded to its e^2
+// term, so a seed good to ~2^-22 lands below 2^-60 before the final rounding.
 //
 // rcp64: for normal, finite x != 0.  Seed: the hardware approximation
-// rcp.approx.ftz.f64 (about 2^-22 relative); two Newton-Raphson steps
-// r <- r + r (1 - x r) square the error each time (2^-44, then rounding).
+// rcp.approx.ftz.f64 (about 2^-22 relative); with e = 1 - x r,
+//   1/x = r / (1 - e) ~ r (1 + e + e^2)         (three FMAs).
 __device__ __forceinline__ double rcp64(double x) {
   double r;
   asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(x));
-  double e = fma(-x, r, 1.0);
-  r = fma(r, e, r);
-  e = fma(-x, r, 1.0);
-  return fma(r, e, r);
+  const double e = fma(-x, r, 1.0);
+  return fma(r, fma(e, e, e), r);
 }
 
-// cbrt64: x^(1/3) for x >= 0.  For 2^-100 <= x < 2^101 the seed is
-// 2^(log2(x)/3) in FP32 (MUFU, about 1e-7 relative), with the FP64 <-> FP32
-// conversions done by integer operations on the IEEE fields (mantissa
-// truncated; exponent re-biased by 1023 - 127 = 896) so that they stay off
-// the FP64 pipe; then one step of Halley's method for y^3 = x,
-//   y <- y (y^3 + 2x) / (2 y^3 + x),
-// whose error shrinks cubically (1e-7 -> below rounding), with the quotient
-// formed by rcp64.  Other x (0, tiny, huge) use the library cube root.
-__device__ __forceinline__ double cbrt64(double x) {
+// FP64 <-> FP32 by integer operations on the IEEE fields (mantissa truncated;
+// exponent re-biased by 1023 - 127 = 896), valid for 2^-100 <= |x| < 2^101,
+// so that the seeds below stay off the FP64 pipe.
+__device__ __forceinline__ float seed_f32(double x) {
   const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
-  if (hi - ((1023u - 100u) << 20) >= (201u << 20)) return cbrt(x);
-  const float xf = __uint_as_float(((hi - (896u << 20)) << 3) | (lo >> 29));
-  float l, yf;
-  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(l) : "f"(xf));
-  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(yf) : "f"(l * (1.0f / 3.0f)));
-  const unsigned yb = __float_as_uint(yf);
-  const double y = __hiloint2double((int)((yb >> 3) + (896u << 20)), (int)(yb << 29));
-  const double y3 = y * y * y;
-  return y * fma(2.0, x, y3) * rcp64(fma(2.0, y3, x));
+  return __uint_as_float(((hi - (896u << 20)) << 3) | (lo >> 29));
+}
+__device__ __forceinline__ double seed_f64(float f) {
+  const unsigned b = __float_as_uint(f);
+  return __hiloint2double((int)((b >> 3) + (896u << 20)), (int)(b << 29));
+}
+// true when 2^-100 <= x < 2^101 (x >= 0 assumed; also false for 0, Inf, NaN)
+__device__ __forceinline__ bool seed_range(double x) {
+  return (unsigned)__double2hiint(x) - ((1023u - 100u) << 20) < (201u << 20);
+}
+
+// sqrt64: sqrt(x) for x >= 0.  Seed z ~ x^(-1/2) from the FP32 MUFU
+// rsqrt.approx; with e = 1 - x z^2,
+//   sqrt(x) = x z (1 - e)^(-1/2) ~ w + w e (1/2 + 3e/8),   w = x z.
+// Arguments outside [2^-100, 2^101) (0 among them) use the library sqrt.
+__device__ __forceinline__ double sqrt64(double x) {
+  if (!seed_range(x)) return sqrt(x);
+  float zf;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(zf) : "f"(seed_f32(x)));
+  const double z = seed_f64(zf);
+  const double e = fma(-x, z * z, 1.0);
+  const double w = x * z;
+  return fma(w, e * fma(0.375, e, 0.5), w);
+}
+
+// cbrt_pair64: c1 = x^(1/3) and c2 = x^(2/3) for x >= 0.  Seed z ~ x^(-1/3)
+// = 2^(-log2(x)/3) in FP32 (MUFU lg2 and ex2); with e = 1 - x z^3,
+//   x^(-1/3) = z (1 - e)^(-1/3) ~ z (1 + u),   u = e (1/3 + 2e/9),
+//   x^(2/3) = x z (1 + u),   x^(1/3) = x^(2/3) z (1 + u).
+// Arguments outside [2^-100, 2^101) (0 among them) use the library cube root.
+__device__ __forceinline__ void cbrt_pair64(double x, double& c1, double& c2) {
+  if (!seed_range(x)) {
+    c1 = cbrt(x);
+    c2 = c1 * c1;
+    return;
+  }
+  float l, zf;
+  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(l) : "f"(seed_f32(x)));
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(zf) : "f"(l * (-1.0f / 3.0f)));
+  const double z = seed_f64(zf);
+  const double w = x * z;                       // ~ x^(2/3)
+  const double e = fma(-w, z * z, 1.0);
+  const double u = e * fma(2.0 / 9.0, e, 1.0 / 3.0);
+  c2 = fma(w, u, w);
+  c1 = c2 * fma(z, u, z);
+}
+
+__device__ __forceinline__ double cbrt64(double x) {
+  double c1, c2;
+  cbrt_pair64(x, c1, c2);
+  return c1;
 }
 
 // Grid arrays on the device (padded, ghost-filled).
@@ -108,6 +150,8 @@ struct Consts {
   double k_lam, k_sgs;             // Cp/Pr, Cp/Pr_sgs
   double C_s;
   double kappa2, kappa4, sigma;
+  double kappa2_half, kappa4_half;  // kappa2 / 2, kappa4 / 2 (exact)
+  double gm1_half, mu_sut;          // (gamma - 1) / 2, mu_ref (1 + S_hat)
   int sigma_is_two_thirds;
   double cfl, dt_fixed;
   double p_inf;
@@ -128,6 +172,10 @@ inline Consts make_consts(const jz_params& p) {
   c.C_s = p.C_s;
   c.kappa2 = p.kappa2;
   c.kappa4 = p.kappa4;
+  c.kappa2_half = 0.5 * p.kappa2;
+  c.kappa4_half = 0.5 * p.kappa4;
+  c.gm1_half = 0.5 * c.gm1;
+  c.mu_sut = c.mu_ref * c.sut_num;
   c.sigma = p.sigma;
   c.sigma_is_two_thirds = fabs(p.sigma - 2.0 / 3.0) < 1e-15 ? 1 : 0;
   c.cfl = p.cfl;
@@ -157,8 +205,8 @@ __device__ __forceinline__ double node_rate(const GridDev& g, const Consts& c, l
                                             double m2, double m3, double e) {
   const double ir = rcp64(rho);
   const double u = m1 * ir, v = m2 * ir, w = m3 * ir;
-  const double pr = c.gm1 * (e - 0.5 * (m1 * u + m2 * v + m3 * w));
-  const double a = sqrt(c.gamma * pr * ir);
+  const double pr = fma(-c.gm1_half, m1 * u + m2 * v + m3 * w, c.gm1 * e);   // (gamma-1)(e - rho|u|^2/2)
+  const double a = sqrt64(c.gamma * pr * ir);
   double lsum = 0.0;
   if (!g.compact) {
     for (int dir = 0; dir < 3; ++dir) {
@@ -172,7 +220,7 @@ __device__ __forceinline__ double node_rate(const GridDev& g, const Consts& c, l
   const float* M = g.Mf + p * kMF;
   for (int dir = 0; dir < 3; ++dir) {
     const double sx = M[3 * dir], sy = M[3 * dir + 1], sz = M[3 * dir + 2];
-    const double lam = fabs(sx * u + sy * v + sz * w) + a * sqrt(sx * sx + sy * sy + sz * sz);
+    const double lam = fabs(sx * u + sy * v + sz * w) + a * sqrt64(sx * sx + sy * sy + sz * sz);
     lsum = dir == 0 ? lam : lsum + lam;
   }
   return lsum * (double)M[MF_IV];
@@ -270,7 +318,7 @@ cudaError_t stats_with(const Dims& d, const Consts& c, const GridDev& g, const S
                        double* part, cudaStream_t st);
 cudaError_t check_volume(const Dims& d, const GridDev& g, int* bad, cudaStream_t st);
 // self-check of rcp64 / cbrt64 (jz_mathcheck.cu)
-cudaError_t math_check(double* dev_maxrel2, cudaStream_t st);
+cudaError_t math_check(double* dev_maxrel3, cudaStream_t st);
 // flow statistics of the axial velocity (jz_stats.cu)
 cudaError_t flow_sample(const Dims& d, const State& q, double* mean, double* m2, long long n, cudaStream_t st);
 cudaError_t flow_final(const Dims& d, const double* mean, const double* m2, long long n, double* out_mean,

@@ -32,11 +32,7 @@ __device__ __forceinline__ bool advanced(const Dims& d, int i, int j) {
 __device__ __forceinline__ void aniso(const Consts& c, const double lam[3], double Lam[3]) {
   double lo[3], hi[3];
   if (c.sigma_is_two_thirds) {
-    for (int d = 0; d < 3; ++d) {
-      const double t = cbrt64(lam[d]);
-      lo[d] = t;
-      hi[d] = t * t;
-    }
+    for (int d = 0; d < 3; ++d) cbrt_pair64(lam[d], lo[d], hi[d]);
   } else {
     for (int d = 0; d < 3; ++d) {
       lo[d] = lam[d] > 0.0 ? pow(lam[d], 1.0 - c.sigma) : 0.0;
@@ -56,11 +52,11 @@ __global__ void __launch_bounds__(kTPB) k_nodal(Dims d, Consts c, GridDev g, Wor
   const double rho = q.q[0][p], m1 = q.q[1][p], m2 = q.q[2][p], m3 = q.q[3][p], e = q.q[4][p];
   const double ir = rcp64(rho);                 // one reciprocal instead of four divisions
   const double u = m1 * ir, v = m2 * ir, ww = m3 * ir;
-  const double pr = c.gm1 * (e - 0.5 * (m1 * u + m2 * v + m3 * ww));
+  const double pr = fma(-c.gm1_half, m1 * u + m2 * v + m3 * ww, c.gm1 * e);   // (gamma-1)(e - rho|u|^2/2)
   const double T = c.gamma * pr * ir;
-  const double a = sqrt(T);
+  const double a = sqrt64(T);
   // Sutherland, eq. (sutherland), with T_inf = 1
-  const double mu = c.mu_ref * (T * a) * c.sut_num * rcp64(T + c.S_hat);
+  const double mu = c.mu_sut * (T * a) * rcp64(T + c.S_hat);
   w.u[p] = u; w.v[p] = v; w.w[p] = ww; w.T[p] = T; w.p[p] = pr; w.mu[p] = mu;
   double lam[3];
   for (int dir = 0; dir < 3; ++dir) {
@@ -89,31 +85,32 @@ __global__ void __launch_bounds__(kTPB) k_viscous(Dims d, Consts c, GridDev g, W
   for (int dir = 0; dir < 3; ++dir)
     for (int cc = 0; cc < 3; ++cc) S[dir][cc] = g.S[3 * dir + cc][p];
   const double iV = g.invV[p];
-  // L[n][j] = d f_n / d x_j = sum_dir (S^dir_j / (2V)) (f_n[+dir] - f_n[-dir])
-  const double h = 0.5 * iV;
-  double St[3][3];
-  for (int dir = 0; dir < 3; ++dir)
-    for (int cc = 0; cc < 3; ++cc) St[dir][cc] = h * S[dir][cc];
-  double L[4][3];
+  // G[n][j] = sum_dir S^dir_j (f_n[+dir] - f_n[-dir]); the gradient is h G with h = 1/(2V),
+  // and h is applied to the few products below instead of to the nine metrics
+  double G[4][3];
   for (int n = 0; n < 4; ++n) {
     double dd[3];
     for (int dir = 0; dir < 3; ++dir) dd[dir] = f[n][p + s[dir]] - f[n][p - s[dir]];
-    for (int jj = 0; jj < 3; ++jj) L[n][jj] = St[0][jj] * dd[0] + St[1][jj] * dd[1] + St[2][jj] * dd[2];
+    for (int jj = 0; jj < 3; ++jj) G[n][jj] = S[0][jj] * dd[0] + S[1][jj] * dd[1] + S[2][jj] * dd[2];
   }
-  // symmetric strain rate, |S|, Smagorinsky eddy viscosity, stresses
-  const double s11 = L[0][0], s22 = L[1][1], s33 = L[2][2];
-  const double s12 = 0.5 * (L[0][1] + L[1][0]), s13 = 0.5 * (L[0][2] + L[2][0]), s23 = 0.5 * (L[1][2] + L[2][1]);
-  const double div = s11 + s22 + s33;
-  const double SS = s11 * s11 + s22 * s22 + s33 * s33 + 2.0 * (s12 * s12 + s13 * s13 + s23 * s23);
-  const double Smod = sqrt(2.0 * SS);
+  const double h = 0.5 * iV;
+  // strain rate s = h sym(G): s_ii = h G_ii, s_ij = (h/2) A_ij with A_ij = G_ij + G_ji, so
+  //   |S| = sqrt(2 s:s) = h sqrt(2 sum G_ii^2 + sum_{i<j} A_ij^2)
+  const double A12 = G[0][1] + G[1][0], A13 = G[0][2] + G[2][0], A23 = G[1][2] + G[2][1];
+  const double Gd = G[0][0] + G[1][1] + G[2][2];
+  const double DG = G[0][0] * G[0][0] + G[1][1] * G[1][1] + G[2][2] * G[2][2];
+  const double AA = A12 * A12 + A13 * A13 + A23 * A23;
   const double mu = w.mu[p];
   const double csd = c.C_s * g.Delta[p];
-  const double mu_sgs = q.q[0][p] * (csd * csd) * Smod;
-  const double m2e = 2.0 * (mu + mu_sgs);
-  const double k_eff = mu * c.k_lam + mu_sgs * c.k_sgs;
-  const double d3 = div * (1.0 / 3.0);
-  const double t11 = m2e * (s11 - d3), t22 = m2e * (s22 - d3), t33 = m2e * (s33 - d3);
-  const double t12 = m2e * s12, t13 = m2e * s13, t23 = m2e * s23;
+  // Smagorinsky eddy viscosity rho (C_s Delta)^2 |S|
+  const double mu_sgs = q.q[0][p] * (csd * csd) * h * sqrt64(fma(2.0, DG, AA));
+  const double mt = mu + mu_sgs;
+  // tau_ii = 2 mt (s_ii - div/3) = (mt/V) (G_ii - Gd/3);  tau_ij = 2 mt s_ij = (mt h) A_ij
+  const double mV = mt * iV, mh = mt * h;
+  const double kh = (mu * c.k_lam + mu_sgs * c.k_sgs) * h;   // k_eff h: heat flux k_eff h G_T
+  const double d3 = Gd * (1.0 / 3.0);
+  const double t11 = mV * (G[0][0] - d3), t22 = mV * (G[1][1] - d3), t33 = mV * (G[2][2] - d3);
+  const double t12 = mh * A12, t13 = mh * A13, t23 = mh * A23;
   const double tau[3][3] = {{t11, t12, t13}, {t12, t22, t23}, {t13, t23, t33}};
   const double vel[3] = {w.u[p], w.v[p], w.w[p]};
   // Cartesian viscous flux in direction jj: [tau_1j, tau_2j, tau_3j, u_i tau_ij + k dT/dx_j]
@@ -122,7 +119,7 @@ __global__ void __launch_bounds__(kTPB) k_viscous(Dims d, Consts c, GridDev g, W
     F[jj][0] = tau[0][jj];
     F[jj][1] = tau[1][jj];
     F[jj][2] = tau[2][jj];
-    F[jj][3] = vel[0] * tau[0][jj] + vel[1] * tau[1][jj] + vel[2] * tau[2][jj] + k_eff * L[3][jj];
+    F[jj][3] = vel[0] * tau[0][jj] + vel[1] * tau[1][jj] + vel[2] * tau[2][jj] + kh * G[3][jj];
   }
   // H^dir -= S^dir_j F_j, as three fused multiply-adds onto the stored E^dir
   for (int dir = 0; dir < 3; ++dir)
@@ -143,17 +140,20 @@ __global__ void __launch_bounds__(kTPB) k_faces(Dims d, Consts c, Work64 w, Stat
   if (!box_coord(b, blockIdx.x * (long long)blockDim.x + threadIdx.x, i, j, k)) return;
   const long long p = pidx(d, i, j, k);
   const long long s[3] = {1, d.sj, d.sk};
+  // Half coefficients (exact: scaling by 1/2) let the face average (L0 + L1)/2 drop its
+  // multiply; the max of the sensors and the clamp at 0 compare bit patterns on the integer
+  // pipe (the sensors are >= 0, and non-negative doubles order like their bits).
   for (int dir = 0; dir < 3; ++dir) {
     const long long sd = s[dir];
-    const double nu0 = w.nu[dir][p], nu1 = w.nu[dir][p + sd];
-    const double eps2 = c.kappa2 * (nu0 >= nu1 ? nu0 : nu1);
-    const double k4 = c.kappa4 - eps2;
-    const double eps4 = k4 > 0.0 ? k4 : 0.0;
-    const double Lf = 0.5 * (w.Lam[dir][p] + w.Lam[dir][p + sd]);
-    // Lf (eps2 d1 - eps4 d3) with d3 = (q2 - qm) - 3 d1, regrouped as
-    // (Lf eps2 + 3 Lf eps4) d1 - Lf eps4 (q2 - qm): two products per face and variable
-    const double b = Lf * eps4;
-    const double a3 = fma(3.0, b, Lf * eps2);
+    const long long nu0 = __double_as_longlong(w.nu[dir][p]), nu1 = __double_as_longlong(w.nu[dir][p + sd]);
+    const double eps2h = c.kappa2_half * __longlong_as_double(nu0 >= nu1 ? nu0 : nu1);
+    const double k4 = c.kappa4_half - eps2h;
+    const double eps4h = __double_as_longlong(k4) > 0 ? k4 : 0.0;
+    const double Ls = w.Lam[dir][p] + w.Lam[dir][p + sd];   // 2 L_f
+    // L_f (eps2 d1 - eps4 d3) with d3 = (q2 - qm) - 3 d1, regrouped as
+    // (L_f eps2 + 3 L_f eps4) d1 - L_f eps4 (q2 - qm): two products per face and variable
+    const double b = Ls * eps4h;
+    const double a3 = fma(3.0, b, Ls * eps2h);
     for (int m = 0; m < 5; ++m) {
       const double* Q = q.q[m];
       const double d1 = Q[p + sd] - Q[p];
@@ -181,10 +181,11 @@ __global__ void __launch_bounds__(kTPB) k_update(Dims d, GridDev g, Work64 w, St
     const long long s[3] = {1, d.sj, d.sk};
     const bool adv = advanced(d, i, j);
     const double hV = 0.5 * g.invV[p];
-    double R[5];
+    double R[5];                     // 2 V RHS; RHS = hV R
     for (int m = 0; m < 5; ++m) {
       // V RHS = (1/2) sum_dir (H+ - H-) - sum_dir (D0 - D-), summed as
-      // (sum H+ - sum H-) - 2 (sum D0 - sum D-), then times 1/(2V)
+      // (sum H+ - sum H-) - 2 (sum D0 - sum D-), then times 1/(2V) (folded into the
+      // update coefficient below)
       const double* H0 = w.H[0][m];
       const double* H1 = w.H[1][m];
       const double* H2 = w.H[2][m];
@@ -195,21 +196,24 @@ __global__ void __launch_bounds__(kTPB) k_update(Dims d, GridDev g, Work64 w, St
       const double hm = (H0[p - s[0]] + H1[p - s[1]]) + H2[p - s[2]];
       const double dp = (D0[p] + D1[p]) + D2[p];
       const double dm = (D0[p - s[0]] + D1[p - s[1]]) + D2[p - s[2]];
-      R[m] = fma(-2.0, dp - dm, hp - hm) * hV;
+      R[m] = fma(-2.0, dp - dm, hp - hm);
     }
     if (MODE == 0) {
-      const double adt = alpha * sc->dt;
+      const double adtV = alpha * sc->dt * hV;
       double qnew[5];
       for (int m = 0; m < 5; ++m) {
-        qnew[m] = adv ? qn.q[m][p] - adt * R[m] : qin.q[m][p];
+        qnew[m] = adv ? qn.q[m][p] - adtV * R[m] : qin.q[m][p];
         qout.q[m][p] = qnew[m];
       }
       if (want_rate && adv) rate = node_rate(g, c, p, qnew[0], qnew[1], qnew[2], qnew[3], qnew[4]);
     } else {
       const long long N = (long long)d.ni * d.nj * d.nk;
-      for (int m = 0; m < 5; ++m) rhs_flat[m * N + t] = adv ? R[m] : 0.0;
+      for (int m = 0; m < 5; ++m) rhs_flat[m * N + t] = adv ? R[m] * hV : 0.0;
     }
-    if (adv) r2 = R[0] * R[0];
+    if (adv) {
+      const double r0 = R[0] * hV;
+      r2 = r0 * r0;
+    }
   }
   if (want_res) {
     // block sum of RHS_rho^2 -> one atomic per block

@@ -91,7 +91,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
         "jz_save_snapshot": ([vp, ctypes.c_char_p], i),
         "jz_load_snapshot": ([vp, ctypes.c_char_p], i),
         "jz_grid_compact": ([vp], i),
-        "jz_check_math": ([ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)], i),
+        "jz_check_math": ([ctypes.POINTER(ctypes.c_double)] * 3, i),
         "jz_stats_begin": ([vp, i], i),
         "jz_stats_sample": ([vp], i),
         "jz_stats_read": ([vp, vp, vp, ctypes.POINTER(ctypes.c_longlong)], i),
@@ -199,10 +199,11 @@ def jz_grid_compact(grid_h) -> None:
 
 
 def jz_check_math():
-    """(max relative error of the library's FP64 reciprocal, of its cube root) on the device."""
-    a, b = ctypes.c_double(), ctypes.c_double()
-    _check(load().jz_check_math(ctypes.byref(a), ctypes.byref(b)))
-    return a.value, b.value
+    """(max relative error of the library's FP64 reciprocal, cube roots, square root) on the
+    device."""
+    a, b, c = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    _check(load().jz_check_math(ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+    return a.value, b.value, c.value
 
 
 def jz_stats_begin(h, every: int) -> None:

@@ -212,14 +212,15 @@ def test_jet_subsample_500_steps_fp64(jz):
     assert e2.max() <= TOL_L2, e2
 
 
-def test_fp64_reciprocal_and_cube_root(jz):
-    """The FP64 form's own reciprocal (Newton-Raphson from the hardware seed) and cube root
-    (Halley from an FP32 seed) against IEEE division and the CUDA cbrt on 2^20 arguments over
-    [1e-30, 1e30]: within 2 and 4 units of 2^-52 relative."""
-    e_rcp, e_cbrt = jz.jz_check_math()
-    print(f"rcp64 max rel err {e_rcp:.3e}, cbrt64 max rel err {e_cbrt:.3e}")
+def test_fp64_reciprocal_roots(jz):
+    """The FP64 form's own reciprocal, cube roots and square root (third-order Householder
+    steps from hardware or FP32 seeds) against IEEE division, the CUDA cbrt and IEEE sqrt on
+    2^20 arguments over [1e-30, 1e30] and 0: within 2, 4 and 2 units of 2^-52 relative."""
+    e_rcp, e_cbrt, e_sqrt = jz.jz_check_math()
+    print(f"rcp64 {e_rcp:.3e}, cbrt_pair64 {e_cbrt:.3e}, sqrt64 {e_sqrt:.3e} max rel err")
     assert e_rcp <= 2 * 2.0 ** -52
     assert e_cbrt <= 4 * 2.0 ** -52
+    assert e_sqrt <= 2 * 2.0 ** -52
 
 
 @pytest.mark.parametrize("shape", [(1, 1, 1), (2, 3, 1), (3, 1, 2)])

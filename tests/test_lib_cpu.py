@@ -73,7 +73,7 @@ def test_argument_errors_do_not_need_a_gpu(lib):
     # entry points beside the hot path
     for name, args in (("jz_grid_compact", [None]), ("jz_stats_begin", [None, 1]), ("jz_stats_sample", [None]),
                        ("jz_stats_end", [None]), ("jz_save_snapshot", [None, b"x"]), ("jz_load_snapshot", [None, b"x"]),
-                       ("jz_check_math", [None, None]), ("jz_compute_metrics", [None]), ("jz_get_state", [None, None])):
+                       ("jz_check_math", [None, None, None]), ("jz_compute_metrics", [None]), ("jz_get_state", [None, None])):
         fn = getattr(lib, name)
         fn.restype = ctypes.c_int
         assert fn(*args) == -1, name
