@@ -41,8 +41,9 @@ FP64_PEAK_TFLOPS = 152 * 4 * 2.07e9 / 1e12
 # the method needs per node (each quantity once).
 # Viscous: 12 differences, 12 metric contractions (60), strain and |S| terms (21), SGS and
 # transport coefficients (12), stresses (9), work + heat flux (21), H^d -= S^d.F (72),
-# sensors (21) = 227.
-FLOPS_PER_POINT = {"nodal": 83, "viscous": 227, "faces": 168, "update": 76}
+# sensors (21) = 227.  Faces: 3 faces x (7 per face + 5 x 7 per variable) = 126.
+# Update: 5 x (5 differences and sums + 2 for the update) + 5 = 40.
+FLOPS_PER_POINT = {"nodal": 83, "viscous": 227, "faces": 126, "update": 40}
 # DRAM bytes per node of a kernel launch from an ncu capture (dram__bytes_read.sum +
 # dram__bytes_write.sum / nodes), scaled to the full launch by its node count;
 # profiles/k_viscous_fp64_jet256x128x64.md: (541.0 + 225.7) MB over 258 x 130 x 66 nodes.

@@ -609,7 +609,7 @@ int jz_create(jz_grid* g, const jz_params* p, void* stream, jz_solver** out) {
       A(s->w.nu[dir], d.Np);
       for (int m = 0; m < 5; ++m) {
         A(s->w.H[dir][m], d.Np);
-        A(s->w.D[dir][m], d.Np);
+        A(s->w.G[dir][m], d.Np);
       }
     }
   }

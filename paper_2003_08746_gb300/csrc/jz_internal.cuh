@@ -150,7 +150,6 @@ struct Consts {
   double k_lam, k_sgs;             // Cp/Pr, Cp/Pr_sgs
   double C_s;
   double kappa2, kappa4, sigma;
-  double kappa2_half, kappa4_half;  // kappa2 / 2, kappa4 / 2 (exact)
   double gm1_half, mu_sut;          // (gamma - 1) / 2, mu_ref (1 + S_hat)
   int sigma_is_two_thirds;
   double cfl, dt_fixed;
@@ -172,8 +171,6 @@ inline Consts make_consts(const jz_params& p) {
   c.C_s = p.C_s;
   c.kappa2 = p.kappa2;
   c.kappa4 = p.kappa4;
-  c.kappa2_half = 0.5 * p.kappa2;
-  c.kappa4_half = 0.5 * p.kappa4;
   c.gm1_half = 0.5 * c.gm1;
   c.mu_sut = c.mu_ref * c.sut_num;
   c.sigma = p.sigma;
@@ -232,7 +229,7 @@ struct Work64 {
   double* Lam[3];
   double* H[3][5];    // transformed inviscid flux, then inviscid - viscous
   double* nu[3];      // pressure sensor per direction
-  double* D[3][5];    // dissipation face flux at n + 1/2 per direction
+  double* G[3][5];    // twice the total face flux at n + 1/2: H_n + H_(n+1) - 2 d_(n+1/2)
 };
 
 struct State {

@@ -101,7 +101,7 @@ extern "C" int jz_residual_noalloc(const jz_grid* g, const jz_params* p, const d
     w.nu[dir] = next();
     for (int m = 0; m < 5; ++m) {
       w.H[dir][m] = next();
-      w.D[dir][m] = next();
+      w.G[dir][m] = next();
     }
   }
   const Consts c = make_consts(*p);

@@ -14,8 +14,11 @@
 //               gradients by the chain rule, strain rate, Smagorinsky eddy
 //               viscosity, stresses and heat flux; H^dir = E^dir - S^dir_j F_j
 //               (in place over E^dir); pressure sensor nu_dir.
-//  C  faces     Turkel-Vatsa dissipation flux d_{n+1/2} for each direction.
-//  D  update    V RHS = sum_dir [delta_dir H^dir - (d_{n+1/2} - d_{n-1/2})],
+//  C  faces     Turkel-Vatsa dissipation flux d_{n+1/2} for each direction,
+//               combined with the face average of H into the doubled total
+//               face flux G_{n+1/2} = H_n + H_{n+1} - 2 d_{n+1/2}.
+//  D  update    V RHS = sum_dir [delta_dir H^dir - (d_{n+1/2} - d_{n-1/2})]
+//                     = (1/2) sum_dir (G_{n+1/2} - G_{n-1/2}),
 //               Q^(l) = Q^n - alpha_l dt RHS on the advanced nodes.
 #include "jz_internal.cuh"
 
@@ -140,25 +143,28 @@ __global__ void __launch_bounds__(kTPB) k_faces(Dims d, Consts c, Work64 w, Stat
   if (!box_coord(b, blockIdx.x * (long long)blockDim.x + threadIdx.x, i, j, k)) return;
   const long long p = pidx(d, i, j, k);
   const long long s[3] = {1, d.sj, d.sk};
-  // Half coefficients (exact: scaling by 1/2) let the face average (L0 + L1)/2 drop its
-  // multiply; the max of the sensors and the clamp at 0 compare bit patterns on the integer
-  // pipe (the sensors are >= 0, and non-negative doubles order like their bits).
   for (int dir = 0; dir < 3; ++dir) {
     const long long sd = s[dir];
+    // the sensor maximum and the clamp at 0 compare bit patterns on the integer pipe (the
+    // sensors are >= 0, and non-negative doubles order like their bits)
     const long long nu0 = __double_as_longlong(w.nu[dir][p]), nu1 = __double_as_longlong(w.nu[dir][p + sd]);
-    const double eps2h = c.kappa2_half * __longlong_as_double(nu0 >= nu1 ? nu0 : nu1);
-    const double k4 = c.kappa4_half - eps2h;
-    const double eps4h = __double_as_longlong(k4) > 0 ? k4 : 0.0;
-    const double Ls = w.Lam[dir][p] + w.Lam[dir][p + sd];   // 2 L_f
-    // L_f (eps2 d1 - eps4 d3) with d3 = (q2 - qm) - 3 d1, regrouped as
-    // (L_f eps2 + 3 L_f eps4) d1 - L_f eps4 (q2 - qm): two products per face and variable
-    const double b = Ls * eps4h;
-    const double a3 = fma(3.0, b, Ls * eps2h);
+    const double eps2 = c.kappa2 * __longlong_as_double(nu0 >= nu1 ? nu0 : nu1);
+    const double k4 = c.kappa4 - eps2;
+    const double eps4 = __double_as_longlong(k4) > 0 ? k4 : 0.0;
+    // d = L_f (eps2 d1 - eps4 d3) with d3 = (q2 - qm) - 3 d1, regrouped as
+    // (L_f eps2 + 3 L_f eps4) d1 - L_f eps4 (q2 - qm); with Ls = 2 L_f the products below
+    // are 2 b and 2 a3, so 2 d = a32 d1 - b2 e3 exactly as scaled
+    const double Ls = w.Lam[dir][p] + w.Lam[dir][p + sd];
+    const double b2 = Ls * eps4;
+    const double a32 = fma(3.0, b2, Ls * eps2);
     for (int m = 0; m < 5; ++m) {
       const double* Q = q.q[m];
       const double d1 = Q[p + sd] - Q[p];
       const double e3 = Q[p + 2 * sd] - Q[p - sd];
-      w.D[dir][m][p] = fma(a3, d1, -(b * e3));
+      // twice the total face flux: (H_n + H_(n+1)) - 2 d_(n+1/2); the centred difference of H
+      // and the dissipation difference then telescope into one difference of this flux
+      const double hs = w.H[dir][m][p] + w.H[dir][m][p + sd];
+      w.G[dir][m][p] = fma(-a32, d1, fma(b2, e3, hs));
     }
   }
 }
@@ -183,20 +189,12 @@ __global__ void __launch_bounds__(kTPB) k_update(Dims d, GridDev g, Work64 w, St
     const double hV = 0.5 * g.invV[p];
     double R[5];                     // 2 V RHS; RHS = hV R
     for (int m = 0; m < 5; ++m) {
-      // V RHS = (1/2) sum_dir (H+ - H-) - sum_dir (D0 - D-), summed as
-      // (sum H+ - sum H-) - 2 (sum D0 - sum D-), then times 1/(2V) (folded into the
-      // update coefficient below)
-      const double* H0 = w.H[0][m];
-      const double* H1 = w.H[1][m];
-      const double* H2 = w.H[2][m];
-      const double* D0 = w.D[0][m];
-      const double* D1 = w.D[1][m];
-      const double* D2 = w.D[2][m];
-      const double hp = (H0[p + s[0]] + H1[p + s[1]]) + H2[p + s[2]];
-      const double hm = (H0[p - s[0]] + H1[p - s[1]]) + H2[p - s[2]];
-      const double dp = (D0[p] + D1[p]) + D2[p];
-      const double dm = (D0[p - s[0]] + D1[p - s[1]]) + D2[p - s[2]];
-      R[m] = fma(-2.0, dp - dm, hp - hm);
+      // V RHS = sum_dir [(H+ - H-)/2 - (d+ - d-)] = (1/2) sum_dir (G(p) - G(p - s_dir)), with
+      // G the doubled total face flux; the 1/(2V) goes into the update coefficient below
+      const double* G0 = w.G[0][m];
+      const double* G1 = w.G[1][m];
+      const double* G2 = w.G[2][m];
+      R[m] = ((G0[p] - G0[p - s[0]]) + (G1[p] - G1[p - s[1]])) + (G2[p] - G2[p - s[2]]);
     }
     if (MODE == 0) {
       const double adtV = alpha * sc->dt * hV;
