@@ -454,14 +454,14 @@ def main():
         solver32.stats_end()
         fs_per = fs_ms / fs_n
         fs_gbs = 48.0 * npts / (fs_per / 1e3) / 1e9
-        # FP64-pipe bound: 9 FP64 instructions per node against 2 per SM per clock
-        fs_inst = 9.0 * npts / (fs_per / 1e3) / 1e12
+        # FP64-pipe bound: 8 FP64 instructions per node against 2 per SM per clock
+        fs_inst = 8.0 * npts / (fs_per / 1e3) / 1e12
         fs_peak = 152 * 2 * 2.07e9 / 1e12
         variants["flow_stats"] = {
             "kernel": "flow_sample", "ms_per_sample": fs_per, "samples": int(fs_n),
             "roofline": {"bound": "alu", "kernel": "flow_sample", "achieved": fs_inst, "peak": fs_peak,
                          "unit": "T FP64-inst/s", "frac": fs_inst / fs_peak, "traffic": None,
-                         "fp64_inst_per_node": 9, "peak_source": "152 SMs x 2 FP64 inst/clk x 2.07 GHz"},
+                         "fp64_inst_per_node": 8, "peak_source": "152 SMs x 2 FP64 inst/clk x 2.07 GHz"},
             "hbm": {"achieved_gbs": fs_gbs, "frac": fs_gbs / hbm_peak, "algorithmic_bytes_per_node": 48}}
         solver32.close()
         v32 = ws * npts * 5 * args.steps / (r32["ms"] / 1e3) / 1e9

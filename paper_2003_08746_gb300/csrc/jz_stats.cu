@@ -8,7 +8,7 @@
 // M2 += (u - mean_old)(u - mean_new)), which stays accurate when the
 // fluctuations are many orders below the mean.  A sample reads rho and
 // rho u_x and rewrites both accumulators: 48 bytes per node, coalesced along
-// i, one sweep.  Its 9 FP64 instructions per node (reciprocal 4, product 1,
+// i, one sweep.  Its 8 FP64 instructions per node (reciprocal 3, product 1,
 // Welford update 4) at 2 per SM per clock take longer than the 48 bytes at
 // HBM speed, so the FP64 pipe bounds it.  The read-out averages mean and
 // rms = sqrt(M2 / n) over the azimuth k for every (i, j).
