@@ -306,8 +306,9 @@ int jz_check_math(double* rcp_max_rel, double* cbrt_max_rel, double* sqrt_max_re
  * rate the next step would use (FP32-flux form), so that continuing from
  * jz_load_snapshot reproduces an uninterrupted run bit for bit.
  * jz_load_snapshot requires the same grid shape and topology and the same
- * parameters (params_hash); the rate is restored only when the precision
- * matches, otherwise the next step reduces it afresh.  The file is created
+ * parameters (params_hash); the rate is restored only into an FP32-flux
+ * solver from an FP32-flux snapshot, otherwise the next step reduces it
+ * afresh (the FP64 form always reduces it in its first stage).  The file is created
  * or truncated by save; `path` is a NUL-terminated file name.
  * Both calls synchronise the solver's stream and allocate a device staging
  * buffer [5][N] (kept by the solver) and 2 x 64 MiB of pinned host memory

@@ -220,35 +220,40 @@ int mark(jz_solver* s, int kind) {
     if (r_) return r_;              \
   } while (0)
 
+// cfl_first: stage 1 of a CFL step; the nodal pass reduces the rate of Q^n (Scalars::rate_max
+// is 0 between FP64 steps) and the time step is set from it before the update.
 int run_stage64(jz_solver* s, const jz::State& in, const jz::State& out, double alpha, int want_res,
-                double* rhs_flat, bool want_rate = false) {
+                double* rhs_flat, bool cfl_first = false) {
   const jz::Dims& d = s->grid->d;
   const jz::GridDev& g = s->grid->g;
-  JZ_RUN(JZ_PROF_NODAL, jz::nodal64(d, s->c, g, s->w, in, s->st));
+  JZ_RUN(JZ_PROF_NODAL, jz::nodal64(d, s->c, g, s->w, in, s->st, cfl_first ? &s->sc->rate_max : nullptr));
+  if (cfl_first) JZ_RUN(JZ_PROF_REDUCE, jz::set_dt(s->c, s->sc, 0, s->st));
   JZ_RUN(JZ_PROF_VISCOUS, jz::viscous64(d, s->c, g, s->w, in, s->st));
   JZ_RUN(JZ_PROF_FACES, jz::faces64(d, s->c, s->w, in, s->st));
-  JZ_RUN(JZ_PROF_UPDATE, jz::update64(d, g, s->w, in, s->qn, out, s->sc, alpha, want_res, rhs_flat, s->st,
-                                      want_rate ? &s->c : nullptr));
+  JZ_RUN(JZ_PROF_UPDATE, jz::update64(d, g, s->w, in, s->qn, out, s->sc, alpha, want_res, rhs_flat, s->st));
   return JZ_OK;
 }
 
 int run_step(jz_solver* s) {
   const jz::Dims& d = s->grid->d;
   const jz::GridDev& g = s->grid->g;
-  // Stage 5 of the previous step left the CFL rate of Q^n behind; after jz_set_state
-  // (or a fixed step) it is reduced here.
-  if (s->c.dt_fixed <= 0.0 && !s->rate_ready)
-    JZ_RUN(JZ_PROF_REDUCE, jz::cfl_rate(d, s->c, g, s->qn, s->sc, s->st));
-  JZ_RUN(JZ_PROF_REDUCE, jz::set_dt(s->c, s->sc, 0, s->st));
+  const bool cfl = s->c.dt_fixed <= 0.0;
+  // CFL rate of Q^n: the FP64 form reduces it in its stage-1 nodal pass, which forms the
+  // spectral radii anyway; the FP32-flux form's stage 5 left it behind, and after
+  // jz_set_state it is reduced here.
+  if (s->fp32 || !cfl) {
+    if (cfl && !s->rate_ready) JZ_RUN(JZ_PROF_REDUCE, jz::cfl_rate(d, s->c, g, s->qn, s->sc, s->st));
+    JZ_RUN(JZ_PROF_REDUCE, jz::set_dt(s->c, s->sc, 0, s->st));
+  }
   jz::State in = s->qn;
   for (int l = 0; l < 5; ++l) {
     jz::State out = (l % 2 == 0) ? s->qa : s->qb;
     int r = JZ_OK;
     if (s->fp32)
       JZ_RUN(JZ_PROF_FUSED32, jz::fused32(d, s->c, s->Mf, in, s->qn, out, s->sc, kAlpha[l], l == 0,
-                                          l == 4 && s->c.dt_fixed <= 0.0, nullptr, s->kchunk, s->st));
+                                          l == 4 && cfl, nullptr, s->kchunk, s->st));
     else
-      r = run_stage64(s, in, out, kAlpha[l], l == 0, nullptr, l == 4 && s->c.dt_fixed <= 0.0);
+      r = run_stage64(s, in, out, kAlpha[l], l == 0, nullptr, l == 0 && cfl);
     if (r) return r;
     if (d.topo == JZ_TOPO_JET) {
       JZ_RUN(JZ_PROF_BC, jz::bc_farfield(d, s->c, g, out, s->st));
@@ -264,7 +269,7 @@ int run_step(jz_solver* s) {
   s->qa = t;
   JZ_RUN(JZ_PROF_REDUCE, jz::set_dt(s->c, s->sc, 1, s->st));
   s->steps += 1;
-  s->rate_ready = s->c.dt_fixed <= 0.0;
+  s->rate_ready = s->fp32 && cfl;
   return JZ_OK;
 }
 
@@ -273,12 +278,13 @@ int run_step(jz_solver* s) {
 // roles of the Q^n and stage buffers swap every step and come back after two; so two steps
 // are captured once per starting buffer (on a private stream, nothing executes while
 // capturing) and replayed with one launch.  Not used while profiling (events between
-// kernels), while flow statistics are sampled, or before the first step has left a CFL rate.
+// kernels), while flow statistics are sampled, or before the first FP32-flux step has left a
+// CFL rate.
 // Any capture failure turns graphs off for the solver; the steps then run as plain launches.
 int graph_two_steps(jz_solver* s, bool* done) {
   *done = false;
   if (s->graphs_off || s->prof || s->fs_every > 0) return JZ_OK;
-  if (s->c.dt_fixed <= 0.0 && !s->rate_ready) return JZ_OK;
+  if (s->fp32 && s->c.dt_fixed <= 0.0 && !s->rate_ready) return JZ_OK;
   int slot = s->gkey[0] == s->qn.q[0] ? 0 : (s->gkey[1] == s->qn.q[0] ? 1 : -1);
   if (slot < 0) {
     slot = s->gexec[0] ? 1 : 0;
@@ -327,7 +333,7 @@ int graph_two_steps(jz_solver* s, bool* done) {
   JZ_CK(cudaGraphLaunch(s->gexec[slot], s->st));
   for (int k = 0; k < JZ_NPROF; ++k) s->launches[k] += s->glaunch[slot][k];
   s->steps += 2;
-  s->rate_ready = s->c.dt_fixed <= 0.0;
+  s->rate_ready = s->fp32 && s->c.dt_fixed <= 0.0;
   *done = true;
   return JZ_OK;
 }
@@ -1110,7 +1116,9 @@ int jz_load_snapshot(jz_solver* s, const char* path) {
   h.t = hd.t;
   h.dt = hd.dt;
   h.res_sum = hd.res_sum;
-  const bool rate_ok = (hd.flags & 1) && hd.precision == s->prm.precision;
+  // a stored rate is the FP32-flux form's (the FP64 form reduces its own in stage 1 and keeps
+  // Scalars::rate_max at 0 between steps)
+  const bool rate_ok = (hd.flags & 1) && hd.precision == s->prm.precision && s->fp32;
   if (rate_ok) h.rate_max = hd.rate;
   JZ_CK(cudaMemcpyAsync(s->sc, &h, sizeof h, cudaMemcpyHostToDevice, s->st));
   JZ_CK(cudaStreamSynchronize(s->st));

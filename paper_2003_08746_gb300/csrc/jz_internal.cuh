@@ -282,16 +282,17 @@ cudaError_t pack_real(const Dims& d, double* const* padded, const double* flat, 
 cudaError_t unpack_real(const Dims& d, double* const* padded, double* flat, int nvar,
                         cudaStream_t st);
 // FP64 stage passes (one kernel each)
+// rate_max != nullptr: also reduce the CFL rate of qin over the advanced nodes into
+// *rate_max (max of (sum_dir lambda_dir) / V; the caller has left it 0)
 cudaError_t nodal64(const Dims& d, const Consts& c, const GridDev& g, const Work64& w, const State& qin,
-                    cudaStream_t st);
+                    cudaStream_t st, double* rate_max = nullptr);
 cudaError_t viscous64(const Dims& d, const Consts& c, const GridDev& g, const Work64& w, const State& qin,
                       cudaStream_t st);
 cudaError_t faces64(const Dims& d, const Consts& c, const Work64& w, const State& qin, cudaStream_t st);
 // stage update (rhs_flat == nullptr) or RHS output to rhs_flat [5][N]
 cudaError_t update64(const Dims& d, const GridDev& g, const Work64& w, const State& qin, const State& qn,
                      const State& qout, const Scalars* sc, double alpha, int want_res, double* rhs_flat,
-                     cudaStream_t st,
-                     const Consts* rate_consts = nullptr);
+                     cudaStream_t st);
 // FP32-flux stage (one fused kernel); Mf = the FP32 metric records (kMF floats per padded node).
 cudaError_t fused32(const Dims& d, const Consts& c, const float* Mf, const State& qin, const State& qn,
                     const State& qout, Scalars* sc, double alpha, int want_res, int want_rate, double* rhs_flat,

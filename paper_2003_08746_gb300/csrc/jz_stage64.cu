@@ -47,34 +47,55 @@ __device__ __forceinline__ void aniso(const Consts& c, const double lam[3], doub
   Lam[2] = lam[2] + lo[2] * (hi[0] + hi[1]);
 }
 
-__global__ void __launch_bounds__(kTPB) k_nodal(Dims d, Consts c, GridDev g, Work64 w, State q) {
+// rate_max != nullptr (stage 1): also the CFL rate of the stage input Q^n over the advanced
+// nodes, max of (lambda_xi + lambda_eta + lambda_zeta) / V, from the spectral radii this pass
+// forms anyway (the same expressions as the stand-alone rate pass), reduced block-wise into
+// *rate_max; the time step is set from it before the stage's update.
+__global__ void __launch_bounds__(kTPB) k_nodal(Dims d, Consts c, GridDev g, Work64 w, State q, double* rate_max) {
   Box b{-kG, -kG, -kG, d.ni + 2 * kG, d.nj + 2 * kG, d.nk + 2 * kG};
   int i, j, k;
-  if (!box_coord(b, blockIdx.x * (long long)blockDim.x + threadIdx.x, i, j, k)) return;
-  const long long p = pidx(d, i, j, k);
-  const double rho = q.q[0][p], m1 = q.q[1][p], m2 = q.q[2][p], m3 = q.q[3][p], e = q.q[4][p];
-  const double ir = rcp64(rho);                 // one reciprocal instead of four divisions
-  const double u = m1 * ir, v = m2 * ir, ww = m3 * ir;
-  const double pr = fma(-c.gm1_half, m1 * u + m2 * v + m3 * ww, c.gm1 * e);   // (gamma-1)(e - rho|u|^2/2)
-  const double T = c.gamma * pr * ir;
-  const double a = sqrt64(T);
-  // Sutherland, eq. (sutherland), with T_inf = 1
-  const double mu = c.mu_sut * (T * a) * rcp64(T + c.S_hat);
-  w.u[p] = u; w.v[p] = v; w.w[p] = ww; w.T[p] = T; w.p[p] = pr; w.mu[p] = mu;
-  double lam[3];
-  for (int dir = 0; dir < 3; ++dir) {
-    const double sx = g.S[3 * dir][p], sy = g.S[3 * dir + 1][p], sz = g.S[3 * dir + 2][p];
-    const double U = sx * u + sy * v + sz * ww;
-    lam[dir] = fabs(U) + a * g.Smag[dir][p];
-    w.H[dir][0][p] = rho * U;
-    w.H[dir][1][p] = m1 * U + pr * sx;
-    w.H[dir][2][p] = m2 * U + pr * sy;
-    w.H[dir][3][p] = m3 * U + pr * sz;
-    w.H[dir][4][p] = (e + pr) * U;
+  double rate = 0.0;
+  if (box_coord(b, blockIdx.x * (long long)blockDim.x + threadIdx.x, i, j, k)) {
+    const long long p = pidx(d, i, j, k);
+    const double rho = q.q[0][p], m1 = q.q[1][p], m2 = q.q[2][p], m3 = q.q[3][p], e = q.q[4][p];
+    const double ir = rcp64(rho);                 // one reciprocal instead of four divisions
+    const double u = m1 * ir, v = m2 * ir, ww = m3 * ir;
+    const double pr = fma(-c.gm1_half, m1 * u + m2 * v + m3 * ww, c.gm1 * e);   // (gamma-1)(e - rho|u|^2/2)
+    const double T = c.gamma * pr * ir;
+    const double a = sqrt64(T);
+    // Sutherland, eq. (sutherland), with T_inf = 1
+    const double mu = c.mu_sut * (T * a) * rcp64(T + c.S_hat);
+    w.u[p] = u; w.v[p] = v; w.w[p] = ww; w.T[p] = T; w.p[p] = pr; w.mu[p] = mu;
+    double lam[3];
+    for (int dir = 0; dir < 3; ++dir) {
+      const double sx = g.S[3 * dir][p], sy = g.S[3 * dir + 1][p], sz = g.S[3 * dir + 2][p];
+      const double U = sx * u + sy * v + sz * ww;
+      lam[dir] = fabs(U) + a * g.Smag[dir][p];
+      w.H[dir][0][p] = rho * U;
+      w.H[dir][1][p] = m1 * U + pr * sx;
+      w.H[dir][2][p] = m2 * U + pr * sy;
+      w.H[dir][3][p] = m3 * U + pr * sz;
+      w.H[dir][4][p] = (e + pr) * U;
+    }
+    if (rate_max && i >= 0 && i < d.ni && j >= 0 && j < d.nj && k >= 0 && k < d.nk && advanced(d, i, j))
+      rate = ((lam[0] + lam[1]) + lam[2]) * g.invV[p];
+    double Lam[3];
+    aniso(c, lam, Lam);
+    w.Lam[0][p] = Lam[0]; w.Lam[1][p] = Lam[1]; w.Lam[2][p] = Lam[2];
   }
-  double Lam[3];
-  aniso(c, lam, Lam);
-  w.Lam[0][p] = Lam[0]; w.Lam[1][p] = Lam[1]; w.Lam[2][p] = Lam[2];
+  if (rate_max) {
+    // block max -> one atomic per block (non-negative doubles order like their bits)
+    __shared__ double redm[kTPB / 32];
+    for (int o = 16; o > 0; o >>= 1) rate = fmax(rate, __shfl_xor_sync(0xffffffffu, rate, o));
+    if ((threadIdx.x & 31) == 0) redm[threadIdx.x >> 5] = rate;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+      double x = threadIdx.x < kTPB / 32 ? redm[threadIdx.x] : 0.0;
+      for (int o = 16; o > 0; o >>= 1) x = fmax(x, __shfl_xor_sync(0xffffffffu, x, o));
+      if (threadIdx.x == 0 && x > 0.0)
+        atomicMax(reinterpret_cast<unsigned long long*>(rate_max), (unsigned long long)__double_as_longlong(x));
+    }
+  }
 }
 
 __global__ void __launch_bounds__(kTPB) k_viscous(Dims d, Consts c, GridDev g, Work64 w, State q) {
@@ -170,18 +191,14 @@ __global__ void __launch_bounds__(kTPB) k_faces(Dims d, Consts c, Work64 w, Stat
 }
 
 // mode 0: stage update; mode 1: write RHS to rhs_flat (unpadded [5][N]).
-// want_rate (stage 5): also the CFL rate of the new state at the advanced nodes, reduced
-// into rate_max for the next step (the boundary conditions applied afterwards touch no
-// advanced node), with the same arithmetic as the stand-alone reduction.
 template <int MODE>
 __global__ void __launch_bounds__(kTPB) k_update(Dims d, GridDev g, Work64 w, State qin, State qn, State qout,
                                                  const Scalars* sc, double alpha, int want_res,
-                                                 double* rhs_flat, double* res_sum, Consts c, int want_rate,
-                                                 double* rate_max) {
+                                                 double* rhs_flat, double* res_sum) {
   Box b{0, 0, 0, d.ni, d.nj, d.nk};
   int i, j, k;
   const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  double r2 = 0.0, rate = 0.0;
+  double r2 = 0.0;
   if (box_coord(b, t, i, j, k)) {
     const long long p = pidx(d, i, j, k);
     const long long s[3] = {1, d.sj, d.sk};
@@ -203,7 +220,6 @@ __global__ void __launch_bounds__(kTPB) k_update(Dims d, GridDev g, Work64 w, St
         qnew[m] = adv ? qn.q[m][p] - adtV * R[m] : qin.q[m][p];
         qout.q[m][p] = qnew[m];
       }
-      if (want_rate && adv) rate = node_rate(g, c, p, qnew[0], qnew[1], qnew[2], qnew[3], qnew[4]);
     } else {
       const long long N = (long long)d.ni * d.nj * d.nk;
       for (int m = 0; m < 5; ++m) rhs_flat[m * N + t] = adv ? R[m] * hV : 0.0;
@@ -225,28 +241,14 @@ __global__ void __launch_bounds__(kTPB) k_update(Dims d, GridDev g, Work64 w, St
       if (threadIdx.x == 0) atomicAdd(res_sum, x);
     }
   }
-  if (MODE == 0 && want_rate) {
-    // block max -> one atomic per block (non-negative doubles order like their bits)
-    __shared__ double redm[kTPB / 32];
-    for (int o = 16; o > 0; o >>= 1) rate = fmax(rate, __shfl_xor_sync(0xffffffffu, rate, o));
-    __syncthreads();
-    if ((threadIdx.x & 31) == 0) redm[threadIdx.x >> 5] = rate;
-    __syncthreads();
-    if (threadIdx.x < 32) {
-      double x = threadIdx.x < kTPB / 32 ? redm[threadIdx.x] : 0.0;
-      for (int o = 16; o > 0; o >>= 1) x = fmax(x, __shfl_xor_sync(0xffffffffu, x, o));
-      if (threadIdx.x == 0 && x > 0.0)
-        atomicMax(reinterpret_cast<unsigned long long*>(rate_max), (unsigned long long)__double_as_longlong(x));
-    }
-  }
 }
 
 }  // namespace
 
 cudaError_t nodal64(const Dims& d, const Consts& c, const GridDev& g, const Work64& w, const State& qin,
-                    cudaStream_t st) {
+                    cudaStream_t st, double* rate_max) {
   const long long n0 = (long long)(d.ni + 2 * kG) * (d.nj + 2 * kG) * (d.nk + 2 * kG);
-  k_nodal<<<blocks_for(n0, kTPB), kTPB, 0, st>>>(d, c, g, w, qin);
+  k_nodal<<<blocks_for(n0, kTPB), kTPB, 0, st>>>(d, c, g, w, qin, rate_max);
   return cudaGetLastError();
 }
 
@@ -265,18 +267,14 @@ cudaError_t faces64(const Dims& d, const Consts& c, const Work64& w, const State
 
 cudaError_t update64(const Dims& d, const GridDev& g, const Work64& w, const State& qin, const State& qn,
                      const State& qout, const Scalars* sc, double alpha, int want_res, double* rhs_flat,
-                     cudaStream_t st, const Consts* rate_consts) {
+                     cudaStream_t st) {
   const long long nr = (long long)d.ni * d.nj * d.nk;
   double* res_sum = const_cast<double*>(&sc->res_sum);
-  double* rate_max = const_cast<double*>(&sc->rate_max);
-  const Consts c = rate_consts ? *rate_consts : Consts{};
-  const int want_rate = rate_consts && !rhs_flat ? 1 : 0;
   if (rhs_flat)
-    k_update<1><<<blocks_for(nr, kTPB), kTPB, 0, st>>>(d, g, w, qin, qn, qout, sc, alpha, 0, rhs_flat, res_sum, c,
-                                                       0, rate_max);
+    k_update<1><<<blocks_for(nr, kTPB), kTPB, 0, st>>>(d, g, w, qin, qn, qout, sc, alpha, 0, rhs_flat, res_sum);
   else
     k_update<0><<<blocks_for(nr, kTPB), kTPB, 0, st>>>(d, g, w, qin, qn, qout, sc, alpha, want_res, nullptr,
-                                                       res_sum, c, want_rate, rate_max);
+                                                       res_sum);
   return cudaGetLastError();
 }
 
