@@ -189,6 +189,39 @@ def test_shear_wave_decay():
     assert np.abs(got - pred).max() < 1e-5 * eps
 
 
+@pytest.mark.parametrize("a", [0.1, 0.02])
+def test_pressure_sensor_and_second_difference_dissipation(a):
+    """Odd-even pressure p_i = p0 (1 + a (-1)^i) at rest, uniform rho, inviscid.
+
+    The sensor |p+ - 2p + p-| / (p+ + 2p + p-) equals a at every node, so
+    eps2 = kappa2 a and eps4 = max(0, kappa4 - kappa2 a) (a = 0.1: the second-difference
+    branch alone; a = 0.02: both).  The centred pressure difference vanishes (p_{i+1} =
+    p_{i-1}), and only the energy mode e' (-1)^i, e' = p0 a / (gamma - 1), is dissipated:
+    Delta1 e = -2 e' (-1)^i, Delta3 e = 8 e' (-1)^i at every face, so
+    V RHS_e = 2 L (2 eps2 + 8 eps4) e' (-1)^i with L the face spectral radius; with u = 0 the
+    three radii of a node are equal (lambda = c h^2), the anisotropic scaling gives 3 lambda
+    for any sigma, and L = (3 h^2 / 2)(c_even + c_odd), c = sqrt(gamma p / rho).
+    """
+    g, grid, h = _line_grid()
+    n = g.ni
+    sgn = (-1.0) ** np.arange(n)
+    p0 = 1.0 / GAMMA
+    one = np.ones((1, 1, n))
+    q = W.conserved(one, 0 * one, 0 * one, 0 * one, (p0 * (1 + a * sgn))[None, None, :])
+    c = O.Consts(W.box_params(Re=math.inf, C_s=0.0))
+    R = O.residual(grid, torch.from_numpy(q), c).numpy()
+    eps2 = c.kappa2 * a
+    eps4 = max(0.0, c.kappa4 - eps2)
+    assert (eps4 == 0.0) == (a == 0.1)
+    L = 1.5 * h ** 2 * (math.sqrt(GAMMA * p0 * (1 + a)) + math.sqrt(GAMMA * p0 * (1 - a)))
+    e1 = p0 * a / (GAMMA - 1.0)
+    expect_e = 2.0 * L * (2.0 * eps2 + 8.0 * eps4) * e1 * sgn / h ** 3
+    assert np.abs(R[:4]).max() < 1e-13
+    assert np.allclose(R[4, 0, 0], expect_e, rtol=1e-12, atol=0.0)
+    # the sign damps the mode: Q - dt RHS shrinks e'
+    assert np.all(R[4, 0, 0] * sgn > 0)
+
+
 def test_heat_flux_diffuses():
     """T = 1 + eps sin(x) at uniform p and rest: de/dt = -kappa sin^2(th)/h^2 T' (heat flows down the gradient).
 
