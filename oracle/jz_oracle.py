@@ -280,7 +280,7 @@ class Grid:
 
 
 # ---------------------------------------------------------------------------
-# One residual evaluation (Algorithm 2, lines Calc(Inv. Flux) .. Calc(RHS))
+# One residual evaluation (Algorithm 2: the steps from the inviscid flux to the RHS)
 # ---------------------------------------------------------------------------
 def primitives(Qp: torch.Tensor, c: Consts):
     """u_i = (rho u_i)/rho; p = (gamma-1)(e - rho|u|^2/2); T = gamma p / rho (p = rho R T, R = 1/gamma)."""

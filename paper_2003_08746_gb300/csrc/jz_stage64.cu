@@ -1,7 +1,9 @@
-// FP64 form of one Runge-Kutta stage (Algorithm 2, lines Calc(Inv. Flux) to
-// Update(Cons., alpha_l)), as four passes over the padded grid.
+// FP64 form of one Runge-Kutta stage (Algorithm 2: the steps from the inviscid
+// flux to the update of the conserved variables with alpha_l), as four passes
+// over the padded grid.
 //
-// The FP64 pipe of a GB300 runs at ~1/70 of its FP32 rate, so this form is
+// The FP64 pipe of a GB300 runs at 1/64 of its FP32 rate (2 against 128 lanes
+// per SM per clock), so this form is
 // bound by FP64 arithmetic, not by HBM.  Each pass therefore computes every
 // nodal or face quantity exactly once and hands it to the next pass through
 // HBM (no halo recomputation); the extra traffic costs far less time than
