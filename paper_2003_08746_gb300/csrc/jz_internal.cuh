@@ -196,8 +196,10 @@ struct Scalars {
 };
 
 // CFL rate of one node, (lambda_xi + lambda_eta + lambda_zeta) / V with
-// lambda_d = |S^d . u| + a |S^d|, from its conserved variables.  Shared by the
-// stand-alone reduction and the stage-5 update so that both give the same bits.
+// lambda_d = |S^d . u| + a |S^d|, from its conserved variables: the stand-alone
+// reduction (first FP32-flux step after jz_set_state, the adjoint's frozen step).
+// The FP64 form's stage-1 nodal pass forms the same expressions from the same
+// primitives.
 __device__ __forceinline__ double node_rate(const GridDev& g, const Consts& c, long long p, double rho, double m1,
                                             double m2, double m3, double e) {
   const double ir = rcp64(rho);
