@@ -145,27 +145,37 @@ def _lam_xi(grid_h, u, a=1.0, sigma=2.0 / 3.0):
     return lx + lx ** (1 - sigma) * 2 * le ** sigma
 
 
-def test_entropy_wave_amplification():
+def _entropy_wave_prediction(n, h, u, dt, c, sigma, eps):
+    th = 2 * math.pi / n
+    Lam = _lam_xi(h, u, sigma=sigma)
+    z = dt * complex(-Lam * c.kappa4 * 16 * math.sin(th / 2) ** 4 / h ** 3, -u / h * math.sin(th))
+    P = 1 + z + z ** 2 / 2 + 3 * z ** 3 / 16 + z ** 4 / 32 + z ** 5 / 128
+    return eps * (P * np.exp(1j * th * np.arange(n))).imag
+
+
+@pytest.mark.parametrize("sigma,n", [(2.0 / 3.0, 32), (0.5, 8)])
+def test_entropy_wave_amplification(sigma, n):
     """rho = 1 + eps sin(x), uniform u and p, inviscid: one step multiplies the mode by P(z).
 
     z = dt [-i (u/h) sin(th) - Lambda kappa4 16 sin^4(th/2) / h^3], th = 2 pi/n,
-    Lambda the anisotropic spectral radius of the base flow (nu = 0 since p is uniform).
+    Lambda the anisotropic spectral radius of the base flow (nu = 0 since p is uniform),
+    for the paper-default exponent sigma = 2/3 (cube-root branch) and, on a coarse line where
+    the dissipation is strong enough to tell them apart, a general exponent.
     """
-    g, grid, h = _line_grid()
-    n, eps, u, dt = g.ni, 1e-6, 0.5, 0.05
+    g, grid, h = _line_grid(n)
+    eps, u, dt = 1e-6, 0.5, 0.05
     x = h * np.arange(n)
     one = np.ones((1, 1, n))
     q = W.conserved(1 + eps * np.sin(x)[None, None, :], u * one, 0 * one, 0 * one, one / GAMMA)
-    prm = W.box_params(Re=math.inf, C_s=0.0, dt_fixed=dt)
+    prm = W.box_params(Re=math.inf, C_s=0.0, dt_fixed=dt, sigma=sigma)
     c = O.Consts(prm)
     Q2, _, _ = O.rk_step(grid, torch.from_numpy(q), c, 0.0)
-    th = 2 * math.pi / n
-    Lam = _lam_xi(h, u)
-    z = dt * complex(-Lam * c.kappa4 * 16 * math.sin(th / 2) ** 4 / h ** 3, -u / h * math.sin(th))
-    P = 1 + z + z ** 2 / 2 + 3 * z ** 3 / 16 + z ** 4 / 32 + z ** 5 / 128
-    pred = eps * (P * np.exp(1j * th * np.arange(n))).imag
     got = (Q2[0, 0, 0] - 1).numpy()
+    pred = _entropy_wave_prediction(n, h, u, dt, c, sigma, eps)
     assert np.abs(got - pred).max() < 1e-5 * eps
+    if sigma != 2.0 / 3.0:   # the coarse case distinguishes the exponent
+        other = _entropy_wave_prediction(n, h, u, dt, c, 2.0 / 3.0, eps)
+        assert np.abs(got - other).max() > 2e-5 * eps
 
 
 def test_shear_wave_decay():
