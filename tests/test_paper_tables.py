@@ -66,3 +66,16 @@ def test_jet_setup_matches_the_printed_conditions():
     # the entrance profile is the tanh shear layer whose plateau is the jet Mach number
     shape = 0.5 * (1.0 + np.tanh((0.5 - r[:, 1:, 0][core]) / (2.0 * prm.theta_mom)))
     assert np.allclose(u / np.sqrt(T) / shape, v["jet_mach"], rtol=1e-13)
+
+
+def test_physical_constants_match_the_printed_values():
+    """Pr, Pr_sgs and the Sutherland constant as printed, in the parameters and in the oracle's
+    derived constants (S1 over the reference temperature)."""
+    from oracle import jz_oracle as O
+
+    v = {k: float(x) for k, x in _rows("paper_constants.txt")}
+    for prm in (W.box_params(), W.jet_params()):
+        assert prm.Pr == v["prandtl"] and prm.Pr_sgs == v["prandtl_sgs"] and prm.S1_K == v["sutherland_S1_K"]
+        c = O.Consts(prm)
+        assert c.Pr == v["prandtl"] and c.Pr_sgs == v["prandtl_sgs"]
+        assert c.S_hat == v["sutherland_S1_K"] / prm.T_ref_K
