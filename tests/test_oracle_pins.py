@@ -432,6 +432,122 @@ def test_inflow_supersonic_core_imposed():
     assert np.allclose(out[1].numpy()[~sup], rho_b * ub, rtol=1e-13)
 
 
+def _forcing_only(grid, c, t, m, f, A=0.01):
+    """Entrance target minus the unforced profile with one nonzero amplitude A_mf: [nk][nj-1]."""
+    c.amp.zero_()
+    base = O.inflow_target(grid, c, t)
+    c.amp[m, f] = A
+    out = O.inflow_target(grid, c, t) - base
+    c.amp.zero_()
+    return out.numpy()
+
+
+@pytest.mark.parametrize("m,f", [(3, 2), (0, 1), (7, 3)])
+def test_inflow_forcing_azimuthal_mode(m, f):
+    """Reading c14, azimuthal structure of the entrance forcing, pinned by a discrete Fourier
+    transform over the nk unique azimuthal points (theta_k = 2 pi k / nk) of every radial line:
+    a single amplitude A_mf puts all of the forcing's energy in azimuthal bins m and nk - m
+    (any other mode number, or a temporal factor that depends on theta, leaks into other
+    bins), and bin m carries the phase phi_mf (a sign slip in m theta conjugates it, and a
+    swap with psi_mf, drawn independently, changes it)."""
+    g, grid, c = _jet(ni=6, nj=40, nk=32)
+    t = 0.37
+    fr = _forcing_only(grid, c, t, m, f)                       # [nk][nj-1]
+    X = np.fft.fft(fr, axis=0) / g.nk                          # per radial line
+    line = np.abs(fr).max(axis=0) > 1e-8                       # lines where g(r) is not negligible
+    assert line.sum() >= 6
+    others = np.ones(g.nk, dtype=bool)
+    others[m] = others[(g.nk - m) % g.nk] = False
+    assert np.abs(X[others][:, line]).max() <= 1e-12 * np.abs(fr).max()
+    # complex bin m = (B/2) e^{i phi} with B real (m > 0); bin 0 = B cos(phi), real
+    B = (2.0 if m > 0 else 1.0) * X[m, line]
+    phi = float(c.phi[m, f]) if m > 0 else 0.0
+    rot = B * np.exp(-1j * phi)
+    assert np.abs(rot.imag).max() <= 1e-12 * np.abs(rot).max()
+
+
+@pytest.mark.parametrize("m,f", [(3, 2), (5, 0)])
+def test_inflow_forcing_frequency_and_temporal_phase(m, f):
+    """Reading c14, time dependence of the entrance forcing: sampled at N = 16 equal steps
+    over T = 1 / (St_f U_j) at one entrance node, the forcing is a pure first harmonic of
+    that period (St not multiplied by U_j, or the wrong St_f, spreads energy into other
+    bins), and the phase of the first harmonic is omega t0 + psi_mf - pi/2, i.e. the
+    temporal phase is psi_mf (a swap with phi_mf fails)."""
+    _, grid, c = _jet(ni=6, nj=40, nk=16)
+    Uj, St = c.jet_mach, c.strouhal[f]
+    T = 1.0 / (St * Uj)
+    N, t0 = 16, 0.123
+    # the entrance node with the largest forcing over the period
+    samples = np.array([_forcing_only(grid, c, t0 + n * T / N, m, f) for n in range(N)])   # [N][nk][nj-1]
+    k, j = np.unravel_index(np.abs(samples).max(axis=0).argmax(), samples.shape[1:])
+    x = samples[:, k, j]
+    X = np.fft.fft(x) / N
+    assert np.abs(X[2:N - 1]).max() <= 1e-12 * np.abs(x).max()
+    assert abs(X[0]) <= 1e-12 * np.abs(x).max()
+    expected = (2.0 * math.pi * St * Uj * t0 + float(c.psi[m, f]) - math.pi / 2.0)
+    # the azimuthal factor cos(m theta + phi) may be negative: compare modulo pi, then its sign
+    d = (np.angle(X[1]) - expected + math.pi / 2.0) % math.pi - math.pi / 2.0
+    assert abs(d) <= 1e-10
+
+
+def test_inflow_forcing_radial_envelope_and_amplitude():
+    """Reading c14, radial envelope and scale of the forcing: on the line of largest response
+    the logarithm of the forcing magnitude is a parabola in r with vertex r = 0.5, curvature
+    -1/0.1^2 (a Gaussian of width 0.1 D centred on the lip), and the vertex value is
+    U_j A |cos(m theta + phi) sin(omega t + psi)| (the forcing scales with U_j A)."""
+    _, grid, c = _jet(ni=6, nj=60, nk=16)
+    m, f, A, t = 2, 1, 0.02, 0.31
+    fr = _forcing_only(grid, c, t, m, f, A=A)
+    X = O.real(grid.xyz_p)[:, :, 1:, 0].numpy()               # [3][nk][nj-1] at i = 0
+    r = np.sqrt(X[1] ** 2 + X[2] ** 2)
+    th = np.arctan2(X[2], X[1])
+    k = int(np.abs(fr).max(axis=1).argmax())
+    sel = np.abs(fr[k]) > 1e-6 * np.abs(fr[k]).max()
+    a2, a1, a0 = np.polyfit(r[k, sel], np.log(np.abs(fr[k, sel])), 2)
+    assert abs(a2 + 100.0) <= 1e-6 * 100.0
+    assert abs(-a1 / (2.0 * a2) - 0.5) <= 1e-8
+    vertex = np.exp(a0 - a1 * a1 / (4.0 * a2))
+    ang = abs(math.cos(m * th[k, 0] + float(c.phi[m, f])) *
+              math.sin(2.0 * math.pi * c.strouhal[f] * c.jet_mach * t + float(c.psi[m, f])))
+    assert abs(vertex - c.jet_mach * A * ang) <= 1e-7 * c.jet_mach * A * ang
+
+
+def test_inflow_forcing_stage_times(monkeypatch):
+    """Reading c14, time at which stage l imposes the entrance: t_n + alpha_l dt, with the
+    low-storage coefficients alpha = (1/4, 1/6, 3/8, 1/2, 1) that the RK amplification pin
+    fixes.  The boundary update of every stage is intercepted; after stage 1 the supersonic
+    entrance nodes (all variables imposed) carry the target at t_n + dt/4 and not at t_n, and
+    after stage 5 the target at t_n + dt."""
+    g, grid, c = _jet(ni=8, nj=40, nk=16, dt_fixed=0.05)
+    c.amp.zero_()
+    c.amp[3, 2] = 0.05                  # strong enough to separate the stage times clearly
+    q = torch.from_numpy(W.jet_state(g))
+    seen = []
+    orig = O.apply_bcs
+
+    def spy(grid_, Q, c_, t):
+        out = orig(grid_, Q, c_, t)
+        seen.append((float(t), out.clone()))
+        return out
+
+    monkeypatch.setattr(O, "apply_bcs", spy)
+    tn, dt = 0.8, 0.05
+    O.rk_step(grid, q, c, tn, dt=torch.as_tensor(dt, dtype=torch.float64))
+    alphas = (0.25, 1.0 / 6.0, 0.375, 0.5, 1.0)
+    assert len(seen) == 5
+    for (ts, _), a in zip(seen, alphas):
+        assert abs(ts - (tn + a * dt)) <= 1e-15
+    ut1 = O.inflow_target(grid, c, tn + 0.25 * dt).numpy()
+    ut0 = O.inflow_target(grid, c, tn).numpy()
+    sup = ut1 >= 1.0
+    got1 = (seen[0][1][1, :, 1:, 0] / seen[0][1][0, :, 1:, 0]).numpy()
+    assert np.abs(got1[sup] - ut1[sup]).max() <= 1e-14
+    assert np.abs(ut1[sup] - ut0[sup]).max() >= 1e-4     # the stage time is resolved
+    ut5 = O.inflow_target(grid, c, tn + dt).numpy()
+    got5 = (seen[4][1][1, :, 1:, 0] / seen[4][1][0, :, 1:, 0]).numpy()
+    assert np.abs(got5[sup & (ut5 >= 1.0)] - ut5[sup & (ut5 >= 1.0)]).max() <= 1e-14
+
+
 def test_centerline_and_ghosts_keep_uniform_state():
     g, grid, c = _jet()
     q = _uniform_state((g.nk, g.nj, g.ni))
