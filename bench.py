@@ -31,6 +31,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 WORKLOAD = "jet1000x400x500"
+PROFILED_STEPS = 4               # steps of the per-kernel profiled pass after the timed region
 SAMPLE = (400, 160, 200)         # CPU sample: same jet recipe, 1/15.6 of the points
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # FP64 peak from unit counts and clock: 152 SMs x 4 FP64 flop/clk/SM (2 DFMA) x 2.07 GHz
@@ -228,61 +229,60 @@ def run_configs_table(args, jz, W, torch):
     return 0
 
 
-def run_paper_meshes(args, jz, W, torch):
-    """Single-GPU throughput on the paper's Table "mesh" shapes (nk = 360 unique azimuthal points).
+def paper_mesh_row(jz, W, torch, name, steps, warmup, forms=("fp64", "fp32flux")):
+    """Single-GPU throughput on one of the paper's Table "mesh" shapes (nk = 360 unique azimuthal
+    points): the FP64 form if its 600 bytes per padded node fit, then the FP32-flux form on the
+    full grid if that fits, else on a compact grid (FP32 metrics only, jz_grid_compact).  Grid
+    and state are built on the device; CUDA events on the solver's stream around `steps` steps
+    after `warmup` steps."""
+    ni, nj = W.PAPER_MESHES[name]
+    nk = 360
+    npts = ni * nj * nk
+    padded = ((ni + 4 + 3) // 4 * 4) * (nj + 4) * (nk + 4)
+    row = {"mesh": name, "shape": [ni, nj, nk], "points": npts, "fp64": None, "fp32flux": None}
+    prm = W.jet_params(seed=2)
+    free, _ = torch.cuda.mem_get_info()
+    if (24 * npts + 144 * padded) > 0.9 * free or 216 * padded > 0.9 * free:
+        return row                                   # grid construction itself does not fit
+    xyz = W.jet_grid_device(ni, nj, nk)
+    grid = jz.Grid(ni, nj, nk, xyz, W.TOPO_JET, metrics=False)
+    del xyz
+    torch.cuda.empty_cache()
+    grid.compute_metrics()
 
-    Per mesh: the FP64 form if its 600 bytes per padded node fit, then the FP32-flux form on the
-    full grid if that fits, else on a compact grid (FP32 metrics only, jz_grid_compact)."""
-    rows = []
-    for name in args.paper_meshes.split(","):
-        ni, nj = W.PAPER_MESHES[name]
-        nk = 360
-        npts = ni * nj * nk
-        padded = ((ni + 4 + 3) // 4 * 4) * (nj + 4) * (nk + 4)
-        row = {"mesh": name, "shape": [ni, nj, nk], "points": npts, "fp64": None, "fp32flux": None}
-        prm = W.jet_params(seed=2)
-        free, _ = torch.cuda.mem_get_info()
-        if (24 * npts + 144 * padded) > 0.9 * free or 216 * padded > 0.9 * free:
-            rows.append(row)                         # grid construction itself does not fit
-            print(json.dumps(row), flush=True)
-            continue
-        xyz = W.jet_grid_device(ni, nj, nk)
-        grid = jz.Grid(ni, nj, nk, xyz, W.TOPO_JET, metrics=False)
-        del xyz
+    def state():
+        x = W.jet_grid_device(ni, nj, nk)
+        q = W.jet_state_device(x)
+        del x
         torch.cuda.empty_cache()
-        grid.compute_metrics()
+        return q
 
-        def state():
-            x = W.jet_grid_device(ni, nj, nk)
-            q = W.jet_state_device(x)
-            del x
-            torch.cuda.empty_cache()
-            return q
+    def timed(prec):
+        q = state()
+        stream = torch.cuda.Stream()
+        s = jz.Solver(grid, prm, prec, stream=stream.cuda_stream)
+        s.set_state(q, 0.0)
+        del q
+        torch.cuda.empty_cache()
+        for _ in range(max(warmup, 1)):
+            s.step(1, stats=False)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        s.step(steps, stats=False)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        st = s.step(0, stats=True)
+        s.close()
+        torch.cuda.empty_cache()
+        return {"ms_per_step": ms, "gpoint_stage_per_s": npts * 5 / (ms / 1e3) / 1e9, "min_p": st.min_p,
+                "steps": steps, "warmup": max(warmup, 1)}
 
-        def timed(prec):
-            q = state()
-            stream = torch.cuda.Stream()
-            s = jz.Solver(grid, prm, prec, stream=stream.cuda_stream)
-            s.set_state(q, 0.0)
-            del q
-            torch.cuda.empty_cache()
-            for _ in range(max(args.warmup, 1)):
-                s.step(1, stats=False)
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            s.step(args.steps, stats=False)
-            e1.record(stream)
-            torch.cuda.synchronize()
-            ms = e0.elapsed_time(e1) / args.steps
-            st = s.step(0, stats=True)
-            s.close()
-            torch.cuda.empty_cache()
-            return {"ms_per_step": ms, "gpoint_stage_per_s": npts * 5 / (ms / 1e3) / 1e9, "min_p": st.min_p}
-
-        free, _ = torch.cuda.mem_get_info()
-        if 456 * padded + 40 * npts + 24 * npts < 0.9 * free:
-            row["fp64"] = timed(jz.JZ_PREC_FP64)
-            row["fp64"]["grid"] = "full"
+    free, _ = torch.cuda.mem_get_info()
+    if "fp64" in forms and 456 * padded + 40 * npts + 24 * npts < 0.9 * free:
+        row["fp64"] = timed(jz.JZ_PREC_FP64)
+        row["fp64"]["grid"] = "full"
+    if "fp32flux" in forms:
         free, _ = torch.cuda.mem_get_info()
         mode = "full"
         if 168 * padded + 40 * npts + 24 * npts > 0.9 * free:
@@ -293,8 +293,16 @@ def run_paper_meshes(args, jz, W, torch):
         if (168 if mode == "full" else 120) * padded + 64 * npts < 0.9 * free:
             row["fp32flux"] = timed(jz.JZ_PREC_FP32FLUX)
             row["fp32flux"]["grid"] = mode
-        grid.close()
-        torch.cuda.empty_cache()
+    grid.close()
+    torch.cuda.empty_cache()
+    return row
+
+
+def run_paper_meshes(args, jz, W, torch):
+    """Single-GPU throughput on the paper's Table "mesh" shapes, one JSON line per mesh."""
+    rows = []
+    for name in args.paper_meshes.split(","):
+        row = paper_mesh_row(jz, W, torch, name, args.steps, args.warmup)
         rows.append(row)
         print(json.dumps(row), flush=True)
     print(json.dumps({"paper_meshes": rows}), flush=True)
@@ -314,6 +322,7 @@ def main():
     ap.add_argument("--fp32-only", action="store_true", help="time only the FP32-flux form (profiling runs)")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint variant")
     ap.add_argument("--no-snapshot", action="store_true", help="skip the snapshot save/load timing")
+    ap.add_argument("--no-mesh-i", action="store_true", help="skip the FP32-flux line on the paper's mesh I")
     ap.add_argument("--adjoint-only", action="store_true", help="one adjoint gradient over --steps steps "
                     "on the 128 x 96 x 64 jet (profiling runs)")
     ap.add_argument("--configs-table", action="store_true", help="GPU FP64 / FP32-flux and oracle 1-thread / "
@@ -364,6 +373,9 @@ def main():
     q_dev = torch.from_numpy(q).cuda()
 
     def timed_form(prec, sample_clocks):
+        """Time args.steps steps as the product runs them (profiling off, so pairs of steps
+        replay as CUDA graphs), then take per-kernel device times from a separate profiled pass
+        of a few more steps (an event after every kernel; graphs off while it runs)."""
         solver = jz.Solver(grid, prm, prec, stream=stream.cuda_stream)
         solver.set_state(q_dev, 0.0)
         torch.cuda.synchronize()
@@ -378,23 +390,25 @@ def main():
         if ws > 1:
             dist.barrier()
         torch.cuda.synchronize()
-        solver.profile(True)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         solver.step(args.steps, stats=False)
         e1.record(stream)
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1)
-        prof = solver.profile_read()
-        solver.profile(False)
+        launches = {k: int(v[1]) for k, v in solver.profile_read().items()}    # timed region's launches
         if ws > 1:
             dist.barrier()
         clocks = sampler.stop() if sampler else None
+        solver.profile(True)
+        solver.step(PROFILED_STEPS, stats=False)
+        prof = solver.profile_read()
+        solver.profile(False)
         stats = solver.step(0, stats=True)   # checks the state is finite and positive
         t_max, _ = aggregate(ms, npts, args.steps, ws)
         final = torch.empty_like(q_dev)
         solver.get_state(final)
-        return solver, dict(ms=t_max, prof=prof, clocks=clocks, stats=stats, final=final)
+        return solver, dict(ms=t_max, prof=prof, launches=launches, clocks=clocks, stats=stats, final=final)
 
     if args.fp32_only:
         solver32, r32 = timed_form(jz.JZ_PREC_FP32FLUX, True)
@@ -435,7 +449,7 @@ def main():
            "faces": (g.ni + 1) * (g.nj + 1) * (g.nk + 1), "update": npts}[top]
     achieved = FLOPS_PER_POINT[top] * pts / (top_ms / top_n / 1e3) / 1e12
     total_prof = sum(v[0] for v in prof.values())
-    launches = int(sum(v[1] for v in prof.values()))
+    launches = int(sum(r64["launches"].values()))
 
     # --- FP32-flux / FP64-state form ------------------------------------------
     variants = {}
@@ -479,8 +493,9 @@ def main():
                          "algorithmic_bytes_per_point_stage": 152},
             "kernels": {k: {"ms_per_launch": v[0] / v[1], "launches": int(v[1]), "share": v[0] / tot32}
                         for k, v in r32["prof"].items() if v[1] > 0},
-            "gpu_launches": int(sum(v[1] for v in r32["prof"].values())),
-            "rel_err_vs_fp64": {"steps": args.warmup + args.steps, "l2": e2.tolist(), "max": em.tolist(),
+            "gpu_launches": int(sum(r32["launches"].values())),
+            "rel_err_vs_fp64": {"steps": args.warmup + args.steps + PROFILED_STEPS, "l2": e2.tolist(),
+                                "max": em.tolist(),
                                 "fields": ["rho", "rho_u", "rho_v", "rho_w", "e"]},
             "speedup_vs_fp64": v32 / value,
         }
@@ -515,14 +530,16 @@ def main():
         sa = jz.Solver(grid_a, pa, jz.JZ_PREC_FP64, stream=stream.cuda_stream)
         sa.set_state(torch.from_numpy(qa).cuda(), 0.0)
         amps = np.asarray(pa.forcing_amp)
-        jz.jz_adjoint_step(sa.h, amps, 20, 20, 0.75)            # warm-up
+        # warm-up gradient over 20 steps, profiled (kernel shares); the timed gradient runs unprofiled
         sa.profile_read()
         sa.profile(True)
+        jz.jz_adjoint_step(sa.h, amps, 20, 20, 0.75)
+        prof_a = sa.profile_read()
+        sa.profile(False)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         Ja, ga_grad = jz.jz_adjoint_step(sa.h, amps, 200, 20, 0.75)
         t_adj = time.perf_counter() - t0
-        prof_a = sa.profile_read()
         sa.close()
         grid_a.close()
         tot_a = sum(v[0] for v in prof_a.values())
@@ -532,7 +549,17 @@ def main():
             "forward_equivalent_gpoint_stage_per_s": ga.npts * 5 * 200 / t_adj / 1e9,
             "J": Ja, "grad_inf": float(np.abs(ga_grad).max()),
             "kernels": {k: {"share": v[0] / tot_a, "launches": int(v[1])} for k, v in prof_a.items() if v[1] > 0},
+            "kernels_from": "a profiled 20-step gradient before the timed one",
         }
+
+    # --- the paper's largest mesh (Table mesh, I: 1700 x 1700 x 361) on one GPU, FP32-flux form ---
+    if not args.no_mesh_i and rank == 0:
+        grid.close()
+        q_dev = None
+        torch.cuda.empty_cache()
+        row = paper_mesh_row(jz, W, torch, "I", 3, 2, forms=("fp32flux",))
+        variants["paper_mesh_I"] = dict(row, note="grid and state built on the device; compact grid (FP32 metrics "
+                                        "only) when the full grid does not fit; CUDA events around 3 steps after 2")
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -556,6 +583,9 @@ def main():
                          "peak_source": "FP64 unit count x max SM clock (152 SMs x 4 flop/clk x 2.07 GHz)"},
             "kernels": {k: {"ms_per_launch": v[0] / v[1], "launches": int(v[1]), "share": v[0] / total_prof}
                         for k, v in prof.items() if v[1] > 0},
+            "kernels_from": f"profiled pass of {PROFILED_STEPS} steps right after the timed region (an event "
+                            "after every kernel); the timed region itself runs as the product does, pairs of "
+                            "steps replayed as CUDA graphs",
             "gpu_launches": launches,
             "clocks": clocks,
             "e2e": {"value": e2e_value, "unit": "Gpoint-stage/s", "h2d_bytes_per_step": state_bytes,

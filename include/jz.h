@@ -332,16 +332,22 @@ int jz_load_snapshot(jz_solver* s, const char* path);
  * are caller-owned DEVICE pointers; the work is queued on `stream` (a
  * cudaStream_t, NULL = legacy default stream) and the call returns without
  * waiting for it.  No device memory is allocated: the scratch is a fixed
- * array of JZ_NOALLOC_SCRATCH_BYTES inside the library, present on every
- * GPU that loads the library until the process exits.  A grid needs
+ * array of JZ_NOALLOC_SCRATCH_BYTES (64 MiB) inside the library, charged on
+ * every device where the library's module holding it is loaded and kept
+ * until the process exits -- with CUDA's lazy module loading (the default
+ * since CUDA 12.2) from the first call on that device, with eager loading
+ * from context creation, whether or not this entry point is used.  q, rhs
+ * and the grid must live on the current device.  A grid needs
  * 256 + 47 * 8 * (padded nodes) bytes, padded nodes = round4(ni+4) *
  * (nj+4) * (nk+4) (about 178,000 padded nodes, e.g. 48 x 48 x 48 real
  * nodes); larger grids are rejected with JZ_ERR_ARG and a message giving
  * the limit.  The first call on a device looks up the scratch address (make
  * it before any stream capture).  All calls on a device share the scratch:
  * calls whose kernels overlap on the GPU race; keep them on one stream.
- * Errors: JZ_ERR_ARG (NULL/host pointers, bad parameters, grid too large),
- * JZ_ERR_STATE (metrics not computed), JZ_ERR_CUDA. */
+ * Errors: JZ_ERR_ARG (NULL/host pointers, pointers or grid on another
+ * device, bad parameters, grid too large), JZ_ERR_STATE (metrics not
+ * computed, compact grid), JZ_ERR_CUDA (including a CUDA error that earlier
+ * work left pending, which is reported and not cleared). */
 #define JZ_NOALLOC_SCRATCH_BYTES (64u * 1024u * 1024u)
 int jz_residual_noalloc(const jz_grid* g, const jz_params* p, const double* q, double* rhs, void* stream);
 

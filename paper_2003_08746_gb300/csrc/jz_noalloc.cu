@@ -15,7 +15,11 @@
 // device (with that device current); the first call should therefore come
 // before any stream capture.  Every call on a device shares the array, so
 // calls whose kernels overlap on the GPU (other streams, other host
-// threads) race with each other; order them on one stream.
+// threads) race with each other; order them on one stream.  The array is
+// charged on every device where this file's module is loaded: with CUDA's
+// lazy module loading (the default since CUDA 12.2) when the first call
+// looks up its address on that device, with eager loading when the
+// library's context is created there.
 #include <mutex>
 
 #include "jz_internal.cuh"
@@ -49,13 +53,16 @@ cudaError_t scratch_address(void** out) {
   return cudaSuccess;
 }
 
-bool on_device(const void* p) {
+// Device of a device (or managed) pointer; -1 for host memory or an unknown pointer.  The
+// caller has checked that no earlier error is pending, so an error raised by the probe itself
+// is the only one cleared here.
+int device_of(const void* p) {
   cudaPointerAttributes a;
   if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
     cudaGetLastError();
-    return false;
+    return -1;
   }
-  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+  return (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) ? a.device : -1;
 }
 
 }  // namespace
@@ -74,8 +81,26 @@ extern "C" int jz_residual_noalloc(const jz_grid* g, const jz_params* p, const d
   if (!(p->gamma > 1.0) || !(p->Re > 0.0) || !(p->Pr > 0.0) || !(p->Pr_sgs > 0.0) || !(p->T_ref_K > 0.0) ||
       !(p->sigma > 0.0 && p->sigma < 1.0))
     return set_error(JZ_ERR_ARG, "jz_residual_noalloc: parameter out of range");
-  if (!on_device(q) || !on_device(rhs))
-    return set_error(JZ_ERR_ARG, "jz_residual_noalloc: q and rhs must be device pointers");
+  // an error left by the caller's earlier work is reported, not cleared by the probes below
+  cudaError_t pend = cudaPeekAtLastError();
+  if (pend != cudaSuccess) {
+    char msg[256];
+    snprintf(msg, sizeof msg, "jz_residual_noalloc: a CUDA error from earlier work is pending: %s",
+             cudaGetErrorString(pend));
+    return set_error(JZ_ERR_CUDA, msg);
+  }
+  int cur = -1;
+  cudaError_t e = cudaGetDevice(&cur);
+  if (e != cudaSuccess) return set_error(JZ_ERR_CUDA, cudaGetErrorString(e));
+  const int dq = device_of(q), dr = device_of(rhs), dg = device_of(gd.V);
+  if (dq < 0 || dr < 0) return set_error(JZ_ERR_ARG, "jz_residual_noalloc: q and rhs must be device pointers");
+  if (dq != cur || dr != cur || dg != cur) {
+    char msg[256];
+    snprintf(msg, sizeof msg,
+             "jz_residual_noalloc: q (device %d), rhs (device %d) and the grid (device %d) must all be on the "
+             "current device %d", dq, dr, dg, cur);
+    return set_error(JZ_ERR_ARG, msg);
+  }
   // scratch: Scalars block, padded state (5 fields), stage work arrays (42 fields)
   const size_t need = kHeader + (size_t)47 * (size_t)d.Np * sizeof(double);
   if (need > kScratchBytes) {
@@ -86,7 +111,7 @@ extern "C" int jz_residual_noalloc(const jz_grid* g, const jz_params* p, const d
     return set_error(JZ_ERR_ARG, msg);
   }
   void* base = nullptr;
-  cudaError_t e = scratch_address(&base);
+  e = scratch_address(&base);
   if (e != cudaSuccess) return set_error(JZ_ERR_CUDA, cudaGetErrorString(e));
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   Scalars* sc = static_cast<Scalars*>(base);

@@ -188,9 +188,20 @@ def jz_residual(h, q, rhs):
     _check(load().jz_residual(h, _ptr(q), _ptr(rhs)))
 
 
+def _stream_handle(stream):
+    """cudaStream_t of a torch.cuda.Stream (its .cuda_stream), a raw handle, or, for None,
+    torch's current stream on the current device."""
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    return int(getattr(stream, "cuda_stream", stream))
+
+
 def jz_residual_noalloc(grid_h, params: jz_params, q, rhs, stream=None):
-    """Residual with the library's fixed scratch array (no device allocation); device q and rhs."""
-    st = ctypes.c_void_p(0 if stream is None else int(stream))
+    """Residual with the library's fixed scratch array (no device allocation); device q and rhs.
+    The work is queued on `stream` (default: torch's current stream), and the call returns
+    without waiting for it."""
+    st = ctypes.c_void_p(_stream_handle(stream))
     _check(load().jz_residual_noalloc(grid_h, ctypes.byref(params), _ptr(q), _ptr(rhs), st))
 
 

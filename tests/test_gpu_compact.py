@@ -6,8 +6,9 @@ import numpy as np
 import pytest
 import torch
 
+from oracle import jz_oracle as O
 from paper_2003_08746_gb300 import workloads as W
-from parity import field_errors
+from parity import field_errors, oracle_grid
 
 pytestmark = pytest.mark.gpu
 
@@ -49,6 +50,22 @@ def test_compact_fixed_dt_bit_identical(jz):
     assert np.array_equal(a, b) and sa.t == sb.t
     # totals: FP64 V against FP32 V widened
     assert np.abs(np.array(sa.totals) - np.array(sb.totals)).max() <= 1e-6 * np.abs(sa.totals).max()
+
+
+@pytest.mark.parametrize("dt_fixed", [0.0, 2e-3])
+def test_compact_grid_against_oracle(jz, dt_fixed):
+    """A compact grid (the form the paper's largest meshes run in) against the FP64 oracle
+    directly: the ragged jet over 20 steps of the FP32-flux form, with the CFL step and with
+    a fixed step, within the form's stated bound 1e-5 per field; the time to 1e-6."""
+    g, q = _jet()
+    prm = W.jet_params(seed=2, dt_fixed=dt_fixed)
+    got, st = _run(jz, g, q, prm, True, 20)
+    ref, t, _, _ = O.run(oracle_grid(g), torch.from_numpy(q), O.Consts(prm), 20)
+    e2, em = field_errors(got, ref.numpy())
+    print(f"compact grid FP32-flux 20 steps vs oracle (dt_fixed={dt_fixed}): rel L2 {e2}, rel max {em}")
+    assert e2.max() <= 1e-5, e2
+    assert em.max() <= 1e-5, em
+    assert abs(st.t - t.item()) <= 1e-6 * t.item()
 
 
 def test_compact_cfl_step(jz):

@@ -745,3 +745,28 @@ def test_station_profile_and_potential_core():
     assert float(x[0]) < expect < float(x[-1])
     assert abs(O.potential_core_length(axis, x, uj) - expect) < 1e-12
     assert O.potential_core_length(torch.full_like(x, uj), x, uj) is None
+
+
+def test_domain_of_dependence_of_one_step():
+    """One RK step on an axial slab of a jet grid (its first or last planes, treated as a grid of
+    its own with entrance and exit conditions at both ends) equals the step of the whole grid
+    bit for bit on every node at least 10 planes from the slab's cut: the first stage changes
+    the cut plane (its metrics and boundary update) and the plane next to it (ghost states
+    within the stencil radius 2), and each of the four later stages carries the difference 2
+    planes further, 9 planes in all.  The difference does reach 6 planes in, so the cut's
+    influence is real and bounded as the stencil predicts."""
+    ni, slab = 40, 24
+    g = W.jet_grid(ni, 20, 8, axial_stretch=True)
+    prm = W.jet_params(seed=2, dt_fixed=2e-3)
+    c = O.Consts(prm)
+    rng = np.random.Generator(np.random.PCG64(8))
+    q = W.jet_state(g) + 2e-3 * rng.standard_normal((5, g.nk, g.nj, g.ni))
+    full, _, _, _ = O.run(_grid(g), torch.from_numpy(q), c, 1, t0=0.3)
+    for sl, cut in ((slice(0, slab), slab - 1), (slice(ni - slab, ni), ni - slab)):
+        xyz = np.ascontiguousarray(g.xyz[..., sl])
+        part, _, _, _ = O.run(O.Grid(slab, g.nj, g.nk, xyz, O.TOPO_JET), torch.from_numpy(
+            np.ascontiguousarray(q[..., sl])), c, 1, t0=0.3)
+        d = (part - full[..., sl]).abs().amax(dim=(0, 1, 2)).numpy()      # per plane of the slab
+        dist = np.abs(np.arange(sl.start, sl.stop) - cut)
+        assert d[dist >= 10].max() == 0.0
+        assert d[dist == 6].max() > 1e-15
