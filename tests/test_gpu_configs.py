@@ -174,10 +174,10 @@ def test_jet128x96x64_adjoint_vs_oracle_reverse_sweep(jz):
     go = go.numpy()
     # J = sum_n dt sum_ik w_ik (p~ - p_inf)^2 is quadratic in a small fluctuation, so its error
     # follows from the state bar: a pressure error delta_p changes J by at most
-    # 2 delta_p sum dt w |p~ - p_inf| <= 2 delta_p sqrt(W J) (Cauchy-Schwarz, W = sum_n dt sum_ik w_ik),
+    # 2 delta_p sum dt w |p~ - p_inf| <= 2 delta_p sqrt(Wt J) (Cauchy-Schwarz, Wt = sum_n dt sum_ik w_ik),
     # with delta_p = 1e-12 p_inf.
-    W = 10 * dt * g.nk * float(obs.w.sum())
-    tol_J = 2.0 * TOL_L2 * oc.p_inf * np.sqrt(W * abs(Jo.item()))
+    Wt = 10 * dt * g.nk * float(obs.w.sum())
+    tol_J = 2.0 * TOL_L2 * oc.p_inf * np.sqrt(Wt * abs(Jo.item()))
     print(f"jet128x96x64 adjoint 10 steps: J {J:.12e} vs {Jo.item():.12e} (bar {tol_J:.2e}), "
           f"grad max err {np.abs(gr - go).max():.2e} of {np.abs(go).max():.2e}")
     assert abs(J - Jo.item()) <= tol_J
