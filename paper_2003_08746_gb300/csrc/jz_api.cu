@@ -109,6 +109,18 @@ struct jz_solver {
   jz::Work64 w{};
   bool fp32 = false;              // JZ_PREC_FP32FLUX form
   const float* Mf = nullptr;      // FP32 metric records (FP32-flux form; the grid's if compact)
+  // FP32-flux form: TMA descriptors of the shadows of qn, qa, qb (the buffers swap roles, so a
+  // descriptor is found by its shadow's address)
+  struct TMap {
+    alignas(64) unsigned char b[128];
+  };
+  TMap tmap[3];
+  const float2* tkey[3] = {nullptr, nullptr, nullptr};
+  const void* tmap_of(const jz::State& q) const {
+    for (int i = 0; i < 3; ++i)
+      if (tkey[i] == q.sh) return tmap[i].b;
+    return nullptr;
+  }
   int kchunk = 0;                 // k planes per CTA of the fused kernel
   bool rate_ready = false;        // a CFL rate of Q^n is in Scalars::rate_max
   jz::Scalars* sc = nullptr;
@@ -186,6 +198,7 @@ int load_state(jz_solver* s, const double* src, jz::State& q) {
   }
   JZ_CK(jz::pack_real(d, q.q, dev, 5, s->st));
   JZ_CK(jz::ghost_fill(d, q.q, 5, s->st));
+  if (s->fp32) JZ_CK(jz::shadow_refresh(d, s->c, q, 1, s->st));
   if (host) JZ_CK(cudaStreamSynchronize(s->st));           // the caller may reuse its host buffer
   return JZ_OK;
 }
@@ -250,7 +263,7 @@ int run_step(jz_solver* s) {
     jz::State out = (l % 2 == 0) ? s->qa : s->qb;
     int r = JZ_OK;
     if (s->fp32)
-      JZ_RUN(JZ_PROF_FUSED32, jz::fused32(d, s->c, s->Mf, in, s->qn, out, s->sc, kAlpha[l], l == 0,
+      JZ_RUN(JZ_PROF_FUSED32, jz::fused32(d, s->c, s->Mf, in, s->tmap_of(in), s->qn, out, s->sc, kAlpha[l], l == 0,
                                           l == 4 && cfl, nullptr, s->kchunk, s->st));
     else
       r = run_stage64(s, in, out, kAlpha[l], l == 0, nullptr, l == 0 && cfl);
@@ -261,6 +274,7 @@ int run_step(jz_solver* s) {
       JZ_RUN(JZ_PROF_BC, jz::bc_axis(d, out, s->st));
     }
     JZ_RUN(JZ_PROF_GHOST, jz::ghost_fill(d, out.q, 5, s->st));
+    if (s->fp32) JZ_RUN(JZ_PROF_GHOST, jz::shadow_refresh(d, s->c, out, 0, s->st));
     in = out;
   }
   // Q^{n+1} is in qa (stage 5 wrote it); it becomes Q^n.
@@ -584,6 +598,13 @@ int jz_create(jz_grid* g, const jz_params* p, void* stream, jz_solver** out) {
   s->fp32 = p->precision == JZ_PREC_FP32FLUX;
   float* own_mf = nullptr;
   if (s->fp32) {
+    jz::State* qs[3] = {&s->qn, &s->qa, &s->qb};
+    for (int i = 0; i < 3; ++i) {
+      double* tmp = nullptr;
+      A(tmp, 3 * (size_t)d.Np);           // three float2 (8-byte) arrays of Np
+      qs[i]->sh = reinterpret_cast<float2*>(tmp);
+      s->tkey[i] = qs[i]->sh;
+    }
     if (g->g.compact) {
       s->Mf = g->g.Mf;                     // the grid's own records
     } else {
@@ -630,6 +651,15 @@ int jz_create(jz_grid* g, const jz_params* p, void* stream, jz_solver** out) {
   if (e != cudaSuccess) {
     delete s;
     return fail(alloc_status(e), "jz_create: device allocation failed: %s", cudaGetErrorString(e));
+  }
+  if (s->fp32) {
+    for (int i = 0; i < 3; ++i) {
+      e = jz::make_shadow_map(d, const_cast<float2*>(s->tkey[i]), s->tmap[i].b);
+      if (e != cudaSuccess) {
+        delete s;
+        return fail(JZ_ERR_CUDA, "jz_create: TMA descriptor of the state shadow: %s", cudaGetErrorString(e));
+      }
+    }
   }
   if (own_mf) {
     e = jz::metrics_to_f32(d, g->g, own_mf, s->st);
@@ -714,8 +744,8 @@ int jz_residual(jz_solver* s, const double* q, double* rhs) {
     if (r) return r;
   }
   if (s->fp32) {
-    JZ_RUN(JZ_PROF_FUSED32, jz::fused32(d, s->c, s->Mf, s->qb, s->qb, s->qb, s->sc, 0.0, 0, 0, dst, s->kchunk,
-                                        s->st));
+    JZ_RUN(JZ_PROF_FUSED32, jz::fused32(d, s->c, s->Mf, s->qb, s->tmap_of(s->qb), s->qb, s->qb, s->sc, 0.0, 0, 0,
+                                        dst, s->kchunk, s->st));
   } else {
     r = run_stage64(s, s->qb, s->qb, 0.0, 0, dst);
     if (r) return r;
@@ -767,6 +797,7 @@ int jz_rk_step(jz_solver* s, int nsteps, jz_step_stats* out) {
   out->min_rho = h.min_rho;
   out->min_p = h.min_p;
   out->steps = s->steps;
+  if (h.wait_timeout) return fail(JZ_ERR_CUDA, "a stage kernel's bounded wait for its TMA copy ran out");
   if (h.nonfinite) return fail(JZ_ERR_NONFINITE, "state holds NaN/Inf or non-positive density/pressure");
   return JZ_OK;
 }
@@ -834,7 +865,7 @@ int jz_adjoint_step(jz_solver* s, const double* forcing_amps, int nsteps, int ck
   }
   A(a.mub, d.Np); A(a.rhob, d.Np); A(a.abar, jz::kNF); A(a.J, 1);
   std::vector<jz::State> ck(nseg), seg(C + 1), stg(4);
-  jz::State wa, wb;
+  jz::State wa{}, wb{};
   for (auto& st : ck) AS(st);
   for (auto& st : seg) AS(st);
   for (auto& st : stg) AS(st);

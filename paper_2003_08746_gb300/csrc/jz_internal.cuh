@@ -192,7 +192,7 @@ struct Scalars {
   double tot[5];
   double min_rho, min_p;
   int nonfinite;
-  int pad_;
+  int wait_timeout;   // set by a kernel whose bounded wait on an asynchronous copy ran out
 };
 
 // CFL rate of one node, (lambda_xi + lambda_eta + lambda_zeta) / V with
@@ -236,6 +236,9 @@ struct Work64 {
 
 struct State {
   double* q[5];
+  // FP32-flux form only: the FP32 shadow of q, three float2 arrays of Np padded nodes
+  // [(rho - 1, e - e_inf), (rho u, rho v), (rho w, p - p_inf)] (null in the FP64 form)
+  float2* sh;
 };
 
 // Adjoint arrays (each Np elements unless noted).
@@ -295,10 +298,19 @@ cudaError_t faces64(const Dims& d, const Consts& c, const Work64& w, const State
 cudaError_t update64(const Dims& d, const GridDev& g, const Work64& w, const State& qin, const State& qn,
                      const State& qout, const Scalars* sc, double alpha, int want_res, double* rhs_flat,
                      cudaStream_t st);
-// FP32-flux stage (one fused kernel); Mf = the FP32 metric records (kMF floats per padded node).
-cudaError_t fused32(const Dims& d, const Consts& c, const float* Mf, const State& qin, const State& qn,
-                    const State& qout, Scalars* sc, double alpha, int want_res, int want_rate, double* rhs_flat,
-                    int kchunk, cudaStream_t st);
+// FP32-flux stage (one fused kernel); Mf = the FP32 metric records (kMF floats per padded node);
+// tm_in = the tensor map of qin's shadow (make_shadow_map).  The stage reads qin's shadow and
+// writes qout and its shadow (or, with rhs_flat, the RHS only).
+cudaError_t fused32(const Dims& d, const Consts& c, const float* Mf, const State& qin, const void* tm_in,
+                    const State& qn, const State& qout, Scalars* sc, double alpha, int want_res, int want_rate,
+                    double* rhs_flat, int kchunk, cudaStream_t st);
+// FP32 shadow of q from its FP64 values: every padded node (full) or only the shell that the
+// boundary conditions and the ghost fill rewrite after a stage (ghost layers and the planes
+// i = 0, ni-1, j = 0, nj-1).
+cudaError_t shadow_refresh(const Dims& d, const Consts& c, const State& q, int full, cudaStream_t st);
+// TMA descriptor (CUtensorMap, 128 bytes, 64-byte aligned) of a shadow: 4-D (Pi, Pj, Pk, 3)
+// of 8-byte elements; returns cudaErrorInvalidValue if the encoder is unavailable or refuses.
+cudaError_t make_shadow_map(const Dims& d, float2* sh, void* tmap128);
 cudaError_t fused32_slots(int* slots);
 int fused32_tile_x();
 int fused32_tile_y();

@@ -117,7 +117,7 @@ extern "C" int jz_residual_noalloc(const jz_grid* g, const jz_params* p, const d
   Scalars* sc = static_cast<Scalars*>(base);
   double* f = reinterpret_cast<double*>(static_cast<unsigned char*>(base) + kHeader);
   auto next = [&]() { double* r = f; f += d.Np; return r; };
-  State qp;
+  State qp{};
   for (int m = 0; m < 5; ++m) qp.q[m] = next();
   Work64 w;
   w.u = next(); w.v = next(); w.w = next(); w.T = next(); w.p = next(); w.mu = next();

@@ -2,16 +2,24 @@
 // in FP32; the state Q, the stage combination Q^n - alpha dt RHS and the
 // totals in FP64.  One fused kernel per stage, one HBM sweep:
 //
-//   read Q^(l-1) (FP64, halo 2), Q^n (FP64, own node), metrics (FP32, halo 1),
-//   write Q^(l) (FP64).
+//   read the FP32 shadow of Q^(l-1) (halo 2, by TMA), Q^n (FP64, own node),
+//   metrics (FP32, halo 1); write Q^(l) (FP64) and its FP32 shadow.
+//
+// The shadow of a state is what the stage's FP32 arithmetic reads of it, kept
+// beside the FP64 state in three float2 arrays per padded node:
+// (rho - 1, e - e_inf), (rho u, rho v), (rho w, p - p_inf).  The offsets keep
+// the FP32 values small in the ambient flow.  The stage that writes Q^(l)
+// writes its shadow; after the boundary conditions and the ghost fill a shell
+// kernel refreshes the shadow of the nodes they rewrote.
 //
 // Each CTA owns a TX x TY tile of (i, j) columns and marches in k.  Shared
-// memory holds a ring of three planes of FP32 primitives (tile + 2-node
-// halo), a ring of two planes of in-plane nodal fluxes, spectral radii and
-// sensors (tile + 1-node halo), the same for the zeta direction (tile only),
-// and the xi/eta dissipation faces of one plane.  Per plane:
-//   (a) the FP64 state of plane k+2 (prefetched into registers one plane
-//       earlier) is converted to FP32 and reduced to primitives,
+// memory holds a ring of four planes of the shadow (tile + 2-node halo; each
+// plane is one 4-D TMA box of 34 x 12 x 1 x 3 float2 landing on an mbarrier),
+// a ring of two planes of in-plane nodal fluxes, spectral radii and sensors
+// (tile + 1-node halo), the same for the zeta direction (tile only), and the
+// xi/eta dissipation faces of one plane.  Per plane:
+//   (a) wait for the shadow of plane k+2 (requested one plane earlier) and
+//       form 1/rho on its points; one thread then requests plane k+3,
 //   (b) every node of plane k+1 within one node of the tile gets its
 //       gradients, viscous and inviscid transformed fluxes H^dir, spectral
 //       radii Lambda^dir and pressure sensors nu^dir; the same threads then
@@ -22,8 +30,14 @@
 // FP64 and FP32) issues ~2 instructions per SM per clock against 128 for
 // FP32, so FP64 -> FP32 conversions are done with integer bit operations
 // (truncation), and FP32 -> FP64 exactly, also with integer operations.
-// Only the offsets rho - 1, e - e_inf (which keep the FP32 values small in
-// the ambient flow) and the final Q^n - dQ are FP64 additions.
+// Only the offsets rho - 1, e - e_inf and the final Q^n - dQ are FP64
+// additions.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <cstring>
+
 #include "jz_internal.cuh"
 
 namespace jz {
@@ -42,12 +56,15 @@ constexpr int NT = NP1;                                      // threads per CTA
 constexpr int NOUT = TX * TY;
 constexpr int NOT = 32 * TY;                                 // output threads: one warp per row
 static_assert(TX <= 32 && NOT <= NT, "one warp per output row");
-constexpr int NLOAD = (NP2 + NT - 1) / NT;                   // halo-2 points per thread
+constexpr int NIR = (NP2 + NT - 1) / NT;                     // halo-2 points per thread (1/rho pass)
 
-// primitive ring: rho' = rho - 1, m1, m2, m3, e' = e - e_inf, 1/rho, p' = p - p_inf
+// shadow ring: per halo-2 point three float2 pairs, as in global memory
+// (rho' = rho - 1, e' = e - e_inf), (m1, m2), (m3, p' = p - p_inf), and 1/rho beside them
 // (u = m/rho and T = gamma p/rho are formed where they are used)
-constexpr int F_R = 0, F_E = 4, F_I = 5, F_P = 6, NPF = 7;
-constexpr int NRING = 4;           // planes k-1 .. k+2: the next plane's conversion needs no barrier
+constexpr int NSH = 3;
+constexpr int NRING = 4;           // planes k-1 .. k+2: the next plane's request needs no barrier
+constexpr int BOX_BYTES = NSH * NP2 * 8;                       // one TMA box (34 x 12 x 1 x 3 float2)
+constexpr int SLOT = ((BOX_BYTES + 127) / 128) * 128 / 8;      // float2 per ring slot, 128-byte aligned
 // in-plane flux ring (tile + 1 halo): H^xi(5), H^eta(5), Lambda^xi, Lambda^eta, nu^xi, nu^eta
 constexpr int X_HX = 0, X_HY = 5, X_LX = 10, X_LY = 11, X_NX = 12, X_NY = 13, NXF = 14;
 // zeta ring (tile): H^zeta(5), Lambda^zeta, nu^zeta, 1/V
@@ -56,11 +73,14 @@ constexpr int Z_HZ = 0, Z_L = 5, Z_N = 6, Z_IV = 7, NZF = 8;
 constexpr int NFX = TY * (TX + 1), NFY = (TY + 1) * TX;
 
 struct Smem {
-  float prim[NRING][NPF][NP2];
+  float2 sh[NRING][SLOT];          // TMA destinations (first member: 128-byte aligned)
+  float ir[NRING][NP2];
   float fxy[2][NXF][NP1];
   float fz[2][NZF][NOUT];
   float dx[5][NFX];
   float dy[5][NFY];
+  unsigned long long bar[NRING];   // one mbarrier per ring slot
+  int fail;                        // a bounded wait ran out in this CTA
 };
 
 struct ConstsF {
@@ -141,12 +161,15 @@ __device__ __forceinline__ void face_flux(const ConstsF& c, float La, float Lb, 
 }
 
 struct Args {
+  CUtensorMap tm;            // shadow of Q^(l-1): 4-D (Pi, Pj, Pk, 3) of float2, box 34 x 12 x 1 x 3
   Dims d;
   ConstsF c;
   const float* M;            // FP32 metric records, kMF floats per padded node
-  const double* qin[5];
+  const double* qin[5];      // FP64 Q^(l-1): copied on the nodes the stage does not advance
   const double* qn[5];
   double* qout[5];
+  float2* sout;              // shadow of Q^(l) [3][Np] (null with rhs)
+  long long Np;
   double* rhs;               // non-null: write RHS [5][N] instead of updating
   Scalars* sc;
   double alpha;
@@ -155,81 +178,65 @@ struct Args {
   int want_rate;
 };
 
-// Halo-2 point loaded by this thread in load pass r: pass r = 0 covers points 0..NT-1;
-// the remaining points (pass r = 1) go first to the threads that have no output node
-// (the warps past the output rows, then the unused lanes of the output warps), then to
-// the lowest threads.  -1: none.
-__device__ __forceinline__ int load_point(int r) {
-  const int t = threadIdx.x;
-  if (r == 0) return t < NP2 ? t : -1;
-  int q;
-  if (t >= NOT) {
-    q = NT + (t - NOT);
-  } else if ((t & 31) >= TX) {
-    q = NT + (NT - NOT) + (t >> 5) * (32 - TX) + ((t & 31) - TX);
-  } else {
-    q = NT + (NT - NOT) + TY * (32 - TX) + t;
+// ---- TMA and mbarrier (inline PTX) ----
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void bar_init(unsigned long long* b, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(count) : "memory");
+}
+// Request the shadow of plane k (padded plane k + 2) of this CTA's halo-2 box into a ring slot;
+// the mbarrier completes when its BOX_BYTES have landed.  Called by one thread.
+__device__ __forceinline__ void request_plane(const Args& A, Smem& sm, int slot, int x0, int y0, int k) {
+  unsigned long long* b = &sm.bar[slot];
+  // the slot's previous contents were read through the generic proxy before the last barrier
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(b)), "r"(BOX_BYTES)
+               : "memory");
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, "
+      "%5}], [%6];" ::"r"(smem_u32(&sm.sh[slot][0])),
+      "l"(reinterpret_cast<unsigned long long>(&A.tm)), "r"(x0), "r"(y0), "r"(k + kG), "r"(0), "r"(smem_u32(b))
+      : "memory");
+}
+// Wait for a slot's mbarrier phase with a bounded number of polls; false if it never completed.
+constexpr int kWaitPolls = 1 << 20;
+__device__ __forceinline__ bool wait_slot(Smem& sm, int slot, unsigned parity) {
+  const unsigned b = smem_u32(&sm.bar[slot]);
+  for (int it = 0; it < kWaitPolls; ++it) {
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(b), "r"(parity)
+        : "memory");
+    if (ok) return true;
   }
-  return q < NP2 ? q : -1;
+  return false;
 }
 
-// Padded index at k = 0 of this thread's halo-2 load points (-1: outside the padded box).
-__device__ __forceinline__ void load_bases(const Args& A, int i0, int j0, long long base[NLOAD]) {
+// Plane k of the CTA starting at k0 - 2 uses ring slot ring(k) for the ((k - k0 + 2) / 4)-th time.
+__device__ __forceinline__ unsigned plane_parity(int k, int k0) { return (unsigned)((k - k0 + 2) >> 2) & 1u; }
+
+// 1/rho on the halo-2 points of a landed shadow plane (rho = rho' + 1).
+__device__ __forceinline__ void inv_rho(Smem& sm, int slot) {
 #pragma unroll
-  for (int r = 0; r < NLOAD; ++r) {
-    const int t = load_point(r);
-    const int i = i0 - 2 + t % H2X, j = j0 - 2 + t / H2X;
-    base[r] = (t >= 0 && in_padded(A.d, i, j)) ? pidx(A.d, i, j, 0) : -1;
+  for (int r = 0; r < NIR; ++r) {
+    const int t = threadIdx.x + r * NT;
+    if (t < NP2) sm.ir[slot][t] = f_rcp(sm.sh[slot][t].x + 1.f);
   }
 }
 
-// Load the FP64 state of plane k at this thread's halo-2 points into registers.
-__device__ __forceinline__ void prefetch(const Args& A, const long long base[NLOAD], int k, double reg[NLOAD][5]) {
-  const long long koff = (long long)k * A.d.sk;
-#pragma unroll
-  for (int r = 0; r < NLOAD; ++r) {
-    if (base[r] >= 0) {
-      const long long p = base[r] + koff;
-#pragma unroll
-      for (int m = 0; m < 5; ++m) reg[r][m] = __ldg(A.qin[m] + p);
-    } else {
-      reg[r][0] = 1.0; reg[r][1] = 0.0; reg[r][2] = 0.0; reg[r][3] = 0.0; reg[r][4] = A.c.e_inf;
-    }
-  }
-}
-
-// Request this thread's halo-2 points of plane k into L2 (no registers held).
-__device__ __forceinline__ void l2_plane(const Args& A, const long long base[NLOAD], int k) {
-  const long long koff = (long long)k * A.d.sk;
-#pragma unroll
-  for (int r = 0; r < NLOAD; ++r)
-    if (base[r] >= 0)
-#pragma unroll
-      for (int m = 0; m < 5; ++m) prefetch_l2(A.qin[m] + base[r] + koff);
-}
-
-// Convert prefetched FP64 state to FP32 primitives in a ring slot.
-__device__ __forceinline__ void store_prims(const Args& A, Smem& sm, int slot, const double reg[NLOAD][5]) {
-  const ConstsF& c = A.c;
-#pragma unroll
-  for (int r = 0; r < NLOAD; ++r) {
-    const int t = load_point(r);
-    if (t >= 0) {
-      const float rp = f64_to_f32(reg[r][0] - 1.0);
-      const float m1 = f64_to_f32(reg[r][1]), m2 = f64_to_f32(reg[r][2]), m3 = f64_to_f32(reg[r][3]);
-      const float ep = f64_to_f32(reg[r][4] - c.e_inf);
-      const float ir = f_rcp(rp + 1.f);
-      const float pp = c.gm1 * (ep - 0.5f * ir * (m1 * m1 + m2 * m2 + m3 * m3));
-      float* P = &sm.prim[slot][0][0];
-      P[F_R * NP2 + t] = rp;
-      P[1 * NP2 + t] = m1;
-      P[2 * NP2 + t] = m2;
-      P[3 * NP2 + t] = m3;
-      P[F_E * NP2 + t] = ep;
-      P[F_I * NP2 + t] = ir;
-      P[F_P * NP2 + t] = pp;
-    }
-  }
+// The three shadow pairs of an FP64 state node (the FP32 values the stage arithmetic uses).
+__device__ __forceinline__ void shadow_of(const ConstsF& c, const double q[5], float2 out[NSH]) {
+  const float rp = f64_to_f32(q[0] - 1.0);
+  const float m1 = f64_to_f32(q[1]), m2 = f64_to_f32(q[2]), m3 = f64_to_f32(q[3]);
+  const float ep = f64_to_f32(q[4] - c.e_inf);
+  const float ir = f_rcp(rp + 1.f);
+  const float pp = c.gm1 * (ep - 0.5f * ir * (m1 * m1 + m2 * m2 + m3 * m3));
+  out[0] = make_float2(rp, ep);
+  out[1] = make_float2(m1, m2);
+  out[2] = make_float2(m3, pp);
 }
 
 // Metric record of one node (three 16-byte loads).
@@ -249,6 +256,21 @@ __device__ __forceinline__ void load_metrics(const Args& A, long long nb, int q,
     return;
   }
   load_record(A.M, nb + (long long)q * A.d.sk, met);
+}
+
+// A landed ring slot: the shadow pairs and 1/rho of its halo-2 points.
+struct Plane {
+  const float2* s;
+  const float* ir;
+};
+__device__ __forceinline__ Plane plane(const Smem& sm, int slot) { return Plane{sm.sh[slot], sm.ir[slot]}; }
+__device__ __forceinline__ float2 P_re(const Plane& P, int c) { return P.s[c]; }              // rho', e'
+__device__ __forceinline__ float2 P_m12(const Plane& P, int c) { return P.s[NP2 + c]; }       // m1, m2
+__device__ __forceinline__ float2 P_m3p(const Plane& P, int c) { return P.s[2 * NP2 + c]; }   // m3, p'
+// The five conserved offsets (rho', m1, m2, m3, e') of a ring point: what the dissipation acts on.
+__device__ __forceinline__ void load_q(const Plane& P, int c, float q[5]) {
+  const float2 a = P_re(P, c), b = P_m12(P, c), d = P_m3p(P, c);
+  q[0] = a.x; q[1] = b.x; q[2] = b.y; q[3] = d.x; q[4] = a.y;
 }
 
 // Nodal fluxes, spectral radii and sensors of one node of plane q (slots
@@ -276,16 +298,15 @@ __device__ void nodal(const Args& A, Smem& sm, long long nb, const float met[kMF
 #pragma unroll
     for (int cc = 0; cc < 3; ++cc) S[dir][cc] = met[3 * dir + cc];
   const float iV = met[MF_IV];
-  const float* P0 = &sm.prim[s_0][0][0];
-  const float* Pm = &sm.prim[s_m][0][0];
-  const float* Pp = &sm.prim[s_p][0][0];
+  const Plane P0 = plane(sm, s_0), Pm = plane(sm, s_m), Pp = plane(sm, s_p);
   // u, v, w, T at a node of the ring (plane P, halo-2 index cc)
-  auto uvwT = [&](const float* P, int cc, float f[4]) {
-    const float ir = P[F_I * NP2 + cc];
-    f[0] = P[1 * NP2 + cc] * ir;
-    f[1] = P[2 * NP2 + cc] * ir;
-    f[2] = P[3 * NP2 + cc] * ir;
-    f[3] = c.gamma * (P[F_P * NP2 + cc] + c.p_inf) * ir;
+  auto uvwT = [&](const Plane& P, int cc, float f[4]) {
+    const float ir = P.ir[cc];
+    const float2 a = P_m12(P, cc), b = P_m3p(P, cc);
+    f[0] = a.x * ir;
+    f[1] = a.y * ir;
+    f[2] = b.x * ir;
+    f[3] = c.gamma * (b.y + c.p_inf) * ir;
   };
   // gradients of u, v, w, T: L[n][j] = sum_dir (S^dir_j / (2V)) (f_{+} - f_{-})
   const float h = 0.5f * iV;
@@ -303,13 +324,14 @@ __device__ void nodal(const Args& A, Smem& sm, long long nb, const float met[kMF
 #pragma unroll
     for (int jj = 0; jj < 3; ++jj) L[n][jj] = h * (S[0][jj] * dx + S[1][jj] * dy + S[2][jj] * dz);
   }
-  const float rho = P0[F_R * NP2 + c2] + 1.f;
-  const float m1 = P0[1 * NP2 + c2], m2 = P0[2 * NP2 + c2], m3 = P0[3 * NP2 + c2];
+  const float2 re0 = P_re(P0, c2), m12 = P_m12(P0, c2), m3p = P_m3p(P0, c2);
+  const float rho = re0.x + 1.f;
+  const float m1 = m12.x, m2 = m12.y, m3 = m3p.x;
   float f0[4];
   uvwT(P0, c2, f0);
   const float u = f0[0], v = f0[1], w = f0[2], T = f0[3];
-  const float pp = P0[F_P * NP2 + c2];
-  const float ep = P0[F_E * NP2 + c2];
+  const float pp = m3p.y;
+  const float ep = re0.y;
   const float a = f_sqrt(T);
   const float mu = c.mu_ref * (T * a) * c.sut_num * f_rcp(T + c.S_hat);
   // strain rate (symmetric), eddy viscosity, stresses
@@ -344,9 +366,9 @@ __device__ void nodal(const Args& A, Smem& sm, long long nb, const float met[kMF
   }
   const float r0 = cbrt_pos(lam[0]), r1 = cbrt_pos(lam[1]), r2 = cbrt_pos(lam[2]);
   // pressure sensors (p' = p - p_inf; denominators add 4 p_inf back)
-  const float* pr0 = P0 + F_P * NP2;
-  const float pxm = pr0[c2 - 1], pxp = pr0[c2 + 1], pym = pr0[c2 - H2X], pyp = pr0[c2 + H2X];
-  const float pzm = Pm[F_P * NP2 + c2], pzp = Pp[F_P * NP2 + c2];
+  const float pxm = P_m3p(P0, c2 - 1).y, pxp = P_m3p(P0, c2 + 1).y;
+  const float pym = P_m3p(P0, c2 - H2X).y, pyp = P_m3p(P0, c2 + H2X).y;
+  const float pzm = P_m3p(Pm, c2).y, pzp = P_m3p(Pp, c2).y;
   const float p4 = 4.f * c.p_inf;
 #pragma unroll
   for (int m = 0; m < 5; ++m) {
@@ -373,7 +395,7 @@ constexpr int NTX = 32 * TY, NTY = 32 * (TY + 1);
 static_assert(TX + 1 <= 32, "xi face row fits a warp");
 
 __device__ void plane_faces(const Args& A, Smem& sm, int s_0, int g) {
-  const float* P = &sm.prim[s_0][0][0];
+  const Plane P = plane(sm, s_0);
   const float* Fx = &sm.fxy[g][0][0];
   for (int task = threadIdx.x; task < NTX + NTY; task += NT) {
     float qm[5], q0[5], q1[5], q2[5], out[5];
@@ -383,10 +405,10 @@ __device__ void plane_faces(const Args& A, Smem& sm, int s_0, int g) {
       const int e = oy * (TX + 1) + fx;
       const int a = (oy + 1) * H1X + fx;           // halo-1 index of the left node
       const int cq = (oy + 2) * H2X + fx + 1;      // halo-2 index of the left node
-#pragma unroll
-      for (int m = 0; m < 5; ++m) {
-        qm[m] = P[m * NP2 + cq - 1]; q0[m] = P[m * NP2 + cq]; q1[m] = P[m * NP2 + cq + 1]; q2[m] = P[m * NP2 + cq + 2];
-      }
+      load_q(P, cq - 1, qm);
+      load_q(P, cq, q0);
+      load_q(P, cq + 1, q1);
+      load_q(P, cq + 2, q2);
       face_flux(A.c, Fx[X_LX * NP1 + a], Fx[X_LX * NP1 + a + 1], Fx[X_NX * NP1 + a], Fx[X_NX * NP1 + a + 1],
                 qm, q0, q1, q2, out);
 #pragma unroll
@@ -397,11 +419,10 @@ __device__ void plane_faces(const Args& A, Smem& sm, int s_0, int g) {
       const int e2 = fy * TX + ox;
       const int a = fy * H1X + ox + 1;             // halo-1 index of the lower node
       const int cq = (fy + 1) * H2X + ox + 2;      // halo-2 index of the lower node
-#pragma unroll
-      for (int m = 0; m < 5; ++m) {
-        qm[m] = P[m * NP2 + cq - H2X]; q0[m] = P[m * NP2 + cq]; q1[m] = P[m * NP2 + cq + H2X];
-        q2[m] = P[m * NP2 + cq + 2 * H2X];
-      }
+      load_q(P, cq - H2X, qm);
+      load_q(P, cq, q0);
+      load_q(P, cq + H2X, q1);
+      load_q(P, cq + 2 * H2X, q2);
       face_flux(A.c, Fx[X_LY * NP1 + a], Fx[X_LY * NP1 + a + H1X], Fx[X_NY * NP1 + a], Fx[X_NY * NP1 + a + H1X],
                 qm, q0, q1, q2, out);
 #pragma unroll
@@ -410,16 +431,13 @@ __device__ void plane_faces(const Args& A, Smem& sm, int s_0, int g) {
   }
 }
 
-__device__ __forceinline__ void load_q(const float* P, int c2, float q[5]) {
-#pragma unroll
-  for (int m = 0; m < 5; ++m) q[m] = P[m * NP2 + c2];
-}
 
 constexpr int kMinBlocks = NT <= 320 ? 2 : 1;
 
-__global__ void __launch_bounds__(NT, kMinBlocks) k_fused32(Args A) {
+__global__ void __launch_bounds__(NT, kMinBlocks) k_fused32(const __grid_constant__ Args A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  Smem& sm = *reinterpret_cast<Smem*>(smem_raw);
+  // TMA destinations need 128-byte alignment; the launch adds 128 bytes of room for it
+  Smem& sm = *reinterpret_cast<Smem*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~(uintptr_t)127);
   const Dims& d = A.d;
   const ConstsF& c = A.c;
   const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY;
@@ -434,25 +452,32 @@ __global__ void __launch_bounds__(NT, kMinBlocks) k_fused32(Args A) {
   const bool adv = outv && (d.topo != JZ_TOPO_JET || (oi >= 1 && oi <= d.ni - 2 && oj >= 1 && oj <= d.nj - 2));
   const int c1 = (oy + 1) * H1X + (ox + 1);
   const int c2 = (oy + 2) * H2X + (ox + 2);
+  // the halo-2 box starts at real (i0 - 2, j0 - 2): padded (i0, j0); x0 * 8 bytes is a multiple
+  // of 16 because TX is even
+  const int x0 = i0, y0 = j0;
 
-  long long lb[NLOAD];
-  load_bases(A, i0, j0, lb);
   long long nb;                                    // halo-1 node of this thread (nodal work)
   {
     const int i = i0 - 1 + t % H1X, j = j0 - 1 + t / H1X;
     nb = in_padded(d, i, j) ? pidx(d, i, j, 0) : -1;
   }
   const long long ob = outv ? pidx(d, oi, oj, 0) : 0;   // output node
-  // prime: planes k0-2, k0-1 into the ring; planes k0 and k0+1 requested into L2
-  {
-    double reg[NLOAD][5];
-    prefetch(A, lb, k0 - 2, reg);
-    store_prims(A, sm, ring(k0 - 2), reg);
-    prefetch(A, lb, k0 - 1, reg);
-    store_prims(A, sm, ring(k0 - 1), reg);
+  // prime: mbarriers, then planes k0-2 .. k0 requested; k0-2 and k0-1 waited for
+  int last_req = k0 - 3;                           // thread 0: last plane requested
+  if (t == 0) {
+    for (int s = 0; s < NRING; ++s) bar_init(&sm.bar[s], 1);
+    sm.fail = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  l2_plane(A, lb, k0);
-  l2_plane(A, lb, k0 + 1);
+  __syncthreads();
+  if (t == 0) {
+    for (int q = k0 - 2; q <= k0; ++q) request_plane(A, sm, ring(q), x0, y0, q);
+    last_req = k0;
+  }
+  for (int q = k0 - 2; q <= k0 - 1; ++q) {
+    if (!wait_slot(sm, ring(q), plane_parity(q, k0))) sm.fail = q + 1000000;
+    inv_rho(sm, ring(q));
+  }
 
   float Hz_prev[5] = {0, 0, 0, 0, 0};   // H^zeta(p-1)
   float Dz_prev[5] = {0, 0, 0, 0, 0};   // d^zeta(p-1/2)
@@ -462,7 +487,8 @@ __global__ void __launch_bounds__(NT, kMinBlocks) k_fused32(Args A) {
   float res = 0.f, rate = 0.f;
 
   for (int p = k0 - 2; p < k1; ++p) {
-    // (a) metrics of plane p+1 (used in (b)); plane p+2 -> ring; prefetch plane p+3
+    // (a) metrics of plane p+1 (used in (b)); the shadow of plane p+2 (requested one plane
+    // earlier) and its 1/rho
     float met[kMF];
     load_metrics(A, nb, p + 1, met);
     // L2 hints one plane ahead: metrics of plane p+2 (next iteration's nodal work)
@@ -479,13 +505,16 @@ __global__ void __launch_bounds__(NT, kMinBlocks) k_fused32(Args A) {
 #pragma unroll
       for (int m = 0; m < 5; ++m) prefetch_l2(A.qn[m] + pq);
     }
-    {
-      double reg[NLOAD][5];
-      prefetch(A, lb, p + 2, reg);                   // L2 hit: requested one plane earlier
-      store_prims(A, sm, ring(p + 2), reg);
-    }
-    if (p + 3 <= k1 + 1) l2_plane(A, lb, p + 3);
+    // after a wait ran out no plane is requested or waited for any more (the CTA finishes on
+    // stale data and the host reports the error)
+    if (sm.fail == 0 && !wait_slot(sm, ring(p + 2), plane_parity(p + 2, k0))) sm.fail = p + 2 + 1000000;
+    inv_rho(sm, ring(p + 2));
     __syncthreads();
+    // the slot of plane p-1 is free: request plane p+3 into it
+    if (t == 0 && p + 3 <= k1 + 1 && sm.fail == 0) {
+      request_plane(A, sm, ring(p + 3), x0, y0, p + 3);
+      last_req = p + 3;
+    }
     // (b) nodal quantities of plane p+1, then the xi/eta faces of plane p
     nodal(A, sm, nb, met, ring(p), ring(p + 1), ring(p + 2), (p + 1) & 1);
     plane_faces(A, sm, ring(p), p & 1);
@@ -494,9 +523,7 @@ __global__ void __launch_bounds__(NT, kMinBlocks) k_fused32(Args A) {
     if (outth) {
       const float* Z0 = &sm.fz[p & 1][0][0];
       const float* Z1 = &sm.fz[(p + 1) & 1][0][0];
-      const float* P0 = &sm.prim[ring(p)][0][0];
-      const float* P1 = &sm.prim[ring(p + 1)][0][0];
-      const float* P2 = &sm.prim[ring(p + 2)][0][0];
+      const Plane P0 = plane(sm, ring(p)), P1 = plane(sm, ring(p + 1)), P2 = plane(sm, ring(p + 2));
       const float Lz1 = Z1[Z_L * NOUT + o], Nz1 = Z1[Z_N * NOUT + o];
       // Q^n of this output node, requested before the zeta-face work that hides its latency
       double qn_r[5];
@@ -536,6 +563,10 @@ __global__ void __launch_bounds__(NT, kMinBlocks) k_fused32(Args A) {
             qnew[m] = qn_r[m] - f32_to_f64(adt * R[m]);
             A.qout[m][pp] = qnew[m];
           }
+          float2 shn[NSH];
+          shadow_of(c, qnew, shn);
+#pragma unroll
+          for (int m = 0; m < NSH; ++m) A.sout[m * A.Np + pp] = shn[m];
           if (A.want_rate) {
             const float rho = f64_to_f32(qnew[0]);
             const float ir = f_rcp(rho);
@@ -543,8 +574,7 @@ __global__ void __launch_bounds__(NT, kMinBlocks) k_fused32(Args A) {
             const float u = m1 * ir, v = m2 * ir, w = m3 * ir;
             const float pr = c.gm1 * (f64_to_f32(qnew[4] - c.e_inf) - 0.5f * (m1 * u + m2 * v + m3 * w)) + c.p_inf;
             const float a = f_sqrt(c.gamma * pr * ir);
-            float ls = 0.f;
-            float mr[kMF];
+            float ls = 0.f;            float mr[kMF];
             load_record(A.M, pp, mr);
 #pragma unroll
             for (int dir = 0; dir < 3; ++dir) {
@@ -556,6 +586,9 @@ __global__ void __launch_bounds__(NT, kMinBlocks) k_fused32(Args A) {
         } else {
 #pragma unroll
           for (int m = 0; m < 5; ++m) A.qout[m][pp] = A.qin[m][pp];
+          A.sout[pp] = P_re(P0, c2);
+          A.sout[A.Np + pp] = P_m12(P0, c2);
+          A.sout[2 * A.Np + pp] = P_m3p(P0, c2);
         }
         if (adv) res += R[0] * R[0];
       }
@@ -569,8 +602,14 @@ __global__ void __launch_bounds__(NT, kMinBlocks) k_fused32(Args A) {
       Lz = Lz1;
       Nz = Nz1;
     }
-    // no barrier here: the next plane's conversion writes ring slot p+3, which no
+    // no barrier here: the next iteration's phase (a) writes 1/rho of ring slot p+3, which no
     // thread reads in this iteration; the barrier after it orders the flux rings.
+  }
+  if (t == 0 && sm.fail != 0) {
+    // a wait ran out: give the copies still in flight a bounded time to land before the CTA's
+    // shared memory is released, then report
+    for (int q = sm.fail - 1000000; q <= last_req; ++q) wait_slot(sm, ring(q), plane_parity(q, k0));
+    atomicOr(&A.sc->wait_timeout, 1);
   }
   if (A.want_res || A.want_rate) {
     __shared__ float red[2][NT / 32];
@@ -592,9 +631,66 @@ __global__ void __launch_bounds__(NT, kMinBlocks) k_fused32(Args A) {
   }
 }
 
-}  // namespace
 
-namespace {
+// FP32 shadow of the FP64 state on every padded node (full) or on the shell that the boundary
+// conditions and the ghost fill rewrite: i in {-2, -1, 0, ni-1, ni, ni+1} (all j, k), then j in
+// {-2, -1, 0, nj-1, nj, nj+1} and k in {-2, -1, nk, nk+1} over the remaining nodes.
+__global__ void k_shadow(Dims d, ConstsF c, State q, int full) {
+  long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  int i, j, k;
+  if (full) {
+    const Box b{-kG, -kG, -kG, d.ni + 2 * kG, d.nj + 2 * kG, d.nk + 2 * kG};
+    if (!box_coord(b, t, i, j, k)) return;
+  } else {
+    const int ii = max(d.ni - 2, 0), ij = max(d.nj - 2, 0);
+    const long long cI = 6LL * (d.nj + 2 * kG) * (d.nk + 2 * kG);
+    const long long cJ = 6LL * ii * (d.nk + 2 * kG);
+    const long long cK = 4LL * ii * ij;
+    int a;
+    if (t < cI) {
+      a = (int)(t % 6);
+      const long long r = t / 6;
+      j = (int)(r % (d.nj + 2 * kG)) - kG;
+      k = (int)(r / (d.nj + 2 * kG)) - kG;
+      i = a < 3 ? a - kG : d.ni - 1 + (a - 3);
+    } else if ((t -= cI) < cJ) {
+      a = (int)(t % 6);
+      const long long r = t / 6;
+      i = 1 + (int)(r % ii);
+      k = (int)(r / ii) - kG;
+      j = a < 3 ? a - kG : d.nj - 1 + (a - 3);
+    } else if ((t -= cJ) < cK) {
+      a = (int)(t % 4);
+      const long long r = t / 4;
+      i = 1 + (int)(r % ii);
+      j = 1 + (int)(r / ii);
+      k = a < 2 ? a - kG : d.nk + (a - 2);
+    } else {
+      return;
+    }
+  }
+  const long long p = pidx(d, i, j, k);
+  double v[5];
+#pragma unroll
+  for (int m = 0; m < 5; ++m) v[m] = q.q[m][p];
+  float2 s[NSH];
+  shadow_of(c, v, s);
+#pragma unroll
+  for (int m = 0; m < NSH; ++m) q.sh[m * d.Np + p] = s[m];
+}
+
+ConstsF make_constsf(const Consts& c) {
+  ConstsF f;
+  f.gamma = (float)c.gamma; f.gm1 = (float)c.gm1; f.mu_ref = (float)c.mu_ref; f.S_hat = (float)c.S_hat;
+  f.sut_num = (float)c.sut_num; f.k_lam = (float)c.k_lam; f.k_sgs = (float)c.k_sgs; f.C_s = (float)c.C_s;
+  f.kappa2 = (float)c.kappa2; f.kappa4 = (float)c.kappa4; f.p_inf = (float)c.p_inf;
+  f.e_inf = c.p_inf / c.gm1;
+  f.ep_inf = (float)(f.e_inf + c.p_inf);
+  return f;
+}
+
+constexpr int kSmemBytes = (int)sizeof(Smem) + 128;    // + room to align the ring to 128 bytes
+static_assert(TX % 2 == 0, "the TMA box must start on a 16-byte boundary (x0 = i0 padded, 8-byte elements)");
 
 // The dynamic shared-memory size above 48 KB must be allowed once per device.
 cudaError_t allow_smem() {
@@ -603,7 +699,7 @@ cudaError_t allow_smem() {
   cudaError_t e0 = cudaGetDevice(&dev);
   if (e0 != cudaSuccess) return e0;
   if (dev < 0 || dev >= 64 || !attr[dev]) {
-    cudaError_t e = cudaFuncSetAttribute(k_fused32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Smem));
+    cudaError_t e = cudaFuncSetAttribute(k_fused32, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
     if (e != cudaSuccess) return e;
     if (dev >= 0 && dev < 64) attr[dev] = true;
   }
@@ -619,31 +715,62 @@ cudaError_t fused32_slots(int* slots) {
   int dev = 0, sms = 0, per = 0;
   e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_fused32, NT, (int)sizeof(Smem));
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_fused32, NT, kSmemBytes);
   if (e != cudaSuccess) return e;
   *slots = sms * (per > 0 ? per : 1);
   return cudaSuccess;
 }
 
-cudaError_t fused32(const Dims& d, const Consts& c, const float* Mf, const State& qin, const State& qn,
-                    const State& qout, Scalars* sc, double alpha, int want_res, int want_rate, double* rhs_flat,
-                    int kchunk, cudaStream_t st) {
-  const int smem = (int)sizeof(Smem);
+cudaError_t make_shadow_map(const Dims& d, float2* sh, void* tmap128) {
+  static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+  if (!encode) {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+    if (e != cudaSuccess) return e;
+    if (q != cudaDriverEntryPointSuccess || !fn) return cudaErrorInvalidValue;
+    encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  }
+  // 8-byte elements (one float2 pair each); rows of Pi, planes of Pi x Pj, three arrays of Np
+  const cuuint64_t dims[4] = {(cuuint64_t)d.Pi, (cuuint64_t)d.Pj, (cuuint64_t)d.Pk, (cuuint64_t)NSH};
+  const cuuint64_t strides[3] = {(cuuint64_t)d.Pi * 8, (cuuint64_t)d.sk * 8, (cuuint64_t)d.Np * 8};
+  const cuuint32_t box[4] = {(cuuint32_t)H2X, (cuuint32_t)H2Y, 1, (cuuint32_t)NSH};
+  const cuuint32_t estr[4] = {1, 1, 1, 1};
+  const CUresult r = encode(static_cast<CUtensorMap*>(tmap128), CU_TENSOR_MAP_DATA_TYPE_UINT64, 4, sh, dims, strides,
+                            box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+cudaError_t shadow_refresh(const Dims& d, const Consts& c, const State& q, int full, cudaStream_t st) {
+  long long n;
+  if (full) {
+    n = (long long)(d.ni + 2 * kG) * (d.nj + 2 * kG) * (d.nk + 2 * kG);
+  } else {
+    const long long ii = std::max(d.ni - 2, 0), ij = std::max(d.nj - 2, 0);
+    n = 6LL * (d.nj + 2 * kG) * (d.nk + 2 * kG) + 6LL * ii * (d.nk + 2 * kG) + 4LL * ii * ij;
+  }
+  k_shadow<<<blocks_for(n, 256), 256, 0, st>>>(d, make_constsf(c), q, full);
+  return cudaGetLastError();
+}
+
+cudaError_t fused32(const Dims& d, const Consts& c, const float* Mf, const State& qin, const void* tm_in,
+                    const State& qn, const State& qout, Scalars* sc, double alpha, int want_res, int want_rate,
+                    double* rhs_flat, int kchunk, cudaStream_t st) {
   cudaError_t e0 = allow_smem();
   if (e0 != cudaSuccess) return e0;
   Args A;
+  std::memcpy(&A.tm, tm_in, sizeof(CUtensorMap));
   A.d = d;
-  A.c.gamma = (float)c.gamma; A.c.gm1 = (float)c.gm1; A.c.mu_ref = (float)c.mu_ref; A.c.S_hat = (float)c.S_hat;
-  A.c.sut_num = (float)c.sut_num; A.c.k_lam = (float)c.k_lam; A.c.k_sgs = (float)c.k_sgs; A.c.C_s = (float)c.C_s;
-  A.c.kappa2 = (float)c.kappa2; A.c.kappa4 = (float)c.kappa4; A.c.p_inf = (float)c.p_inf;
-  A.c.e_inf = c.p_inf / c.gm1;
-  A.c.ep_inf = (float)(A.c.e_inf + c.p_inf);
+  A.c = make_constsf(c);
   A.M = Mf;
   for (int m = 0; m < 5; ++m) {
     A.qin[m] = qin.q[m];
     A.qn[m] = qn.q[m];
     A.qout[m] = qout.q[m];
   }
+  A.sout = qout.sh;
+  A.Np = d.Np;
   A.rhs = rhs_flat;
   A.sc = sc;
   A.alpha = alpha;
@@ -651,7 +778,7 @@ cudaError_t fused32(const Dims& d, const Consts& c, const float* Mf, const State
   A.want_res = want_res;
   A.want_rate = want_rate;
   dim3 grid((d.ni + TX - 1) / TX, (d.nj + TY - 1) / TY, (d.nk + A.kchunk - 1) / A.kchunk);
-  k_fused32<<<grid, NT, smem, st>>>(A);
+  k_fused32<<<grid, NT, kSmemBytes, st>>>(A);
   return cudaGetLastError();
 }
 
