@@ -55,6 +55,15 @@ extern "C" {
 #define JZ_PREC_FP64      0   /* every operation in FP64                      */
 #define JZ_PREC_FP32FLUX  1   /* fluxes, dissipation, SGS in FP32; state,
                                  stage combination and totals in FP64        */
+#define JZ_PREC_FP64PAIR  2   /* FP64 state, stage combination and totals;
+                                 fluxes, dissipation, SGS in double-float
+                                 arithmetic (pairs of FP32, ~48 bits) on the
+                                 FP32 pipes: the FP64 form's results within
+                                 its 1e-12 parity bar at FP32-pipe rates.
+                                 Same memory as JZ_PREC_FP64 plus 152 bytes
+                                 per padded node (metric and state copies).
+                                 jz_adjoint_step on such a solver runs the
+                                 FP64 passes.                                 */
 
 #define JZ_N_MODES 8          /* azimuthal forcing modes m = 0..7            */
 #define JZ_N_FREQ  4          /* forcing frequencies (Strouhal numbers)      */
@@ -83,7 +92,7 @@ typedef struct jz_params {
     double forcing_phi[JZ_N_MODES * JZ_N_FREQ];   /* azimuthal phase phi[m][f] */
     double forcing_psi[JZ_N_MODES * JZ_N_FREQ];   /* temporal phase psi[m][f]  */
     double strouhal[JZ_N_FREQ];
-    int precision;      /* JZ_PREC_FP64 or JZ_PREC_FP32FLUX                   */
+    int precision;      /* JZ_PREC_FP64, JZ_PREC_FP32FLUX or JZ_PREC_FP64PAIR */
 } jz_params;
 
 /* Per-call statistics returned by jz_rk_step. */

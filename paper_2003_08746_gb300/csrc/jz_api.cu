@@ -108,6 +108,9 @@ struct jz_solver {
   jz::State qn{}, qa{}, qb{};
   jz::Work64 w{};
   bool fp32 = false;              // JZ_PREC_FP32FLUX form
+  bool pair = false;              // JZ_PREC_FP64PAIR form (double-float stage passes)
+  jz::DFMetrics mdf{};            // pair form: double-float copies of the metrics
+  jz::QDF qdf{};                  // pair form: double-float copy of the stage input
   const float* Mf = nullptr;      // FP32 metric records (FP32-flux form; the grid's if compact)
   // FP32-flux form: TMA descriptors of the shadows of qn, qa, qb (the buffers swap roles, so a
   // descriptor is found by its shadow's address)
@@ -239,6 +242,15 @@ int run_stage64(jz_solver* s, const jz::State& in, const jz::State& out, double 
                 double* rhs_flat, bool cfl_first = false) {
   const jz::Dims& d = s->grid->d;
   const jz::GridDev& g = s->grid->g;
+  if (s->pair) {
+    JZ_RUN(JZ_PROF_NODAL, jz::nodal_df(d, s->c, s->mdf, s->w, s->qdf, in, s->st,
+                                       cfl_first ? &s->sc->rate_max : nullptr));
+    if (cfl_first) JZ_RUN(JZ_PROF_REDUCE, jz::set_dt(s->c, s->sc, 0, s->st));
+    JZ_RUN(JZ_PROF_VISCOUS, jz::viscous_df(d, s->c, s->mdf, s->w, s->qdf, s->st));
+    JZ_RUN(JZ_PROF_FACES, jz::faces_df(d, s->c, s->w, s->qdf, s->st));
+    JZ_RUN(JZ_PROF_UPDATE, jz::update_df(d, g, s->w, in, s->qn, out, s->sc, alpha, want_res, rhs_flat, s->st));
+    return JZ_OK;
+  }
   JZ_RUN(JZ_PROF_NODAL, jz::nodal64(d, s->c, g, s->w, in, s->st, cfl_first ? &s->sc->rate_max : nullptr));
   if (cfl_first) JZ_RUN(JZ_PROF_REDUCE, jz::set_dt(s->c, s->sc, 0, s->st));
   JZ_RUN(JZ_PROF_VISCOUS, jz::viscous64(d, s->c, g, s->w, in, s->st));
@@ -574,7 +586,7 @@ int jz_create(jz_grid* g, const jz_params* p, void* stream, jz_solver** out) {
       !(p->S1_K >= 0.0) || !(p->C_s >= 0.0) || !(p->kappa2 >= 0.0) || !(p->kappa4 >= 0.0) ||
       !(p->sigma > 0.0 && p->sigma < 1.0) || !(p->cfl > 0.0) || !(p->dt_fixed >= 0.0))
     return fail(JZ_ERR_ARG, "jz_create: parameter out of range");
-  if (p->precision != JZ_PREC_FP64 && p->precision != JZ_PREC_FP32FLUX)
+  if (p->precision != JZ_PREC_FP64 && p->precision != JZ_PREC_FP32FLUX && p->precision != JZ_PREC_FP64PAIR)
     return fail(JZ_ERR_ARG, "jz_create: unknown precision %d", p->precision);
   if (g->g.compact && p->precision != JZ_PREC_FP32FLUX)
     return fail(JZ_ERR_STATE, "jz_create: a compact grid (FP32 metrics only) takes the FP32-flux form only");
@@ -630,6 +642,19 @@ int jz_create(jz_grid* g, const jz_params* p, void* stream, jz_solver** out) {
     if (tiles * best > 30LL * slots) best = std::max<long long>(1, 30LL * slots / tiles);
     s->kchunk = (d.nk + best - 1) / best;
   } else {
+    s->pair = p->precision == JZ_PREC_FP64PAIR;
+    if (s->pair) {
+      auto P = [&](float2*& dst) {
+        double* tmp = nullptr;
+        A(tmp, d.Np);                      // one float2 (8 bytes) per padded node
+        dst = reinterpret_cast<float2*>(tmp);
+      };
+      for (int c9 = 0; c9 < 9; ++c9) P(s->mdf.S[c9]);
+      for (int c3 = 0; c3 < 3; ++c3) P(s->mdf.Smag[c3]);
+      P(s->mdf.invV);
+      P(s->mdf.Delta);
+      for (int m = 0; m < 5; ++m) A(s->qdf.q[m], d.Np);
+    }
     A(s->w.u, d.Np); A(s->w.v, d.Np); A(s->w.w, d.Np); A(s->w.T, d.Np); A(s->w.p, d.Np); A(s->w.mu, d.Np);
     for (int dir = 0; dir < 3; ++dir) {
       A(s->w.Lam[dir], d.Np);
@@ -659,6 +684,14 @@ int jz_create(jz_grid* g, const jz_params* p, void* stream, jz_solver** out) {
         delete s;
         return fail(JZ_ERR_CUDA, "jz_create: TMA descriptor of the state shadow: %s", cudaGetErrorString(e));
       }
+    }
+  }
+  if (s->pair) {
+    e = jz::metrics_to_df(d, g->g, s->mdf, s->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->st);
+    if (e != cudaSuccess) {
+      delete s;
+      return fail(JZ_ERR_CUDA, "jz_create: double-float metrics: %s", cudaGetErrorString(e));
     }
   }
   if (own_mf) {

@@ -234,6 +234,18 @@ struct Work64 {
   double* G[3][5];    // twice the total face flux at n + 1/2: H_n + H_(n+1) - 2 d_(n+1/2)
 };
 
+// Pair form (JZ_PREC_FP64PAIR): double-float copies of the metrics (float2 hi/lo per padded
+// node) and of the stage input Q (in FP64-sized arrays, two FP32 each).
+struct DFMetrics {
+  float2* S[9];
+  float2* Smag[3];
+  float2* invV;
+  float2* Delta;
+};
+struct QDF {
+  double* q[5];
+};
+
 struct State {
   double* q[5];
   // FP32-flux form only: the FP32 shadow of q, three float2 arrays of Np padded nodes
@@ -314,6 +326,17 @@ cudaError_t make_shadow_map(const Dims& d, float2* sh, void* tmap128);
 cudaError_t fused32_slots(int* slots);
 int fused32_tile_x();
 int fused32_tile_y();
+// Pair form of the FP64 stage (jz_stagedf.cu): the four passes in double-float arithmetic,
+// the stage combination in FP64.
+cudaError_t metrics_to_df(const Dims& d, const GridDev& g, const DFMetrics& M, cudaStream_t st);
+cudaError_t nodal_df(const Dims& d, const Consts& c, const DFMetrics& M, const Work64& w, const QDF& qdf,
+                     const State& qin, cudaStream_t st, double* rate_max = nullptr);
+cudaError_t viscous_df(const Dims& d, const Consts& c, const DFMetrics& M, const Work64& w, const QDF& qdf,
+                       cudaStream_t st);
+cudaError_t faces_df(const Dims& d, const Consts& c, const Work64& w, const QDF& qdf, cudaStream_t st);
+cudaError_t update_df(const Dims& d, const GridDev& g, const Work64& w, const State& qin, const State& qn,
+                      const State& qout, const Scalars* sc, double alpha, int want_res, double* rhs_flat,
+                      cudaStream_t st);
 // boundary conditions (jet), in this order after every stage
 cudaError_t bc_farfield(const Dims& d, const Consts& c, const GridDev& g, const State& q, cudaStream_t st);
 cudaError_t bc_inout(const Dims& d, const Consts& c, const Inflow& in, const State& q, const Scalars* sc,

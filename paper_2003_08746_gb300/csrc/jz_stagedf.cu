@@ -1,0 +1,327 @@
+// Pair form of the FP64 stage: the four passes of jz_stage64.cu (nodal, viscous, faces,
+// update; Algorithm 2's inviscid flux, dissipation, viscous flux, RHS and Update(Cons, alpha_l))
+// with every flux, dissipation and SGS operation in double-float arithmetic (jz_df.cuh: pairs
+// of FP32 numbers, ~48 significant bits) and the stage combination Q^n - alpha dt RHS in FP64.
+// The state stays FP64; the nodal pass reads it once and leaves a double-float copy for the
+// dissipation of the faces pass; the intermediate fields are double-float pairs (float2) in the
+// FP64 form's work arrays (same size); the metrics are a double-float copy made when the solver
+// is created.
+//
+// The passes are launched on 3-D grids (64 x 4 threads per block along i and j, one block row
+// per k), so no pass divides a flat index.
+#include "jz_df.cuh"
+#include "jz_internal.cuh"
+
+namespace jz {
+namespace {
+
+constexpr int BX = 64, BY = 4;
+
+// node of a 3-D launch over the box [i0, i0 + ei) x [j0, j0 + ej) x [k0, k0 + ek)
+__device__ __forceinline__ bool node3(int i0, int j0, int k0, int ei, int ej, int& i, int& j, int& k) {
+  const int x = blockIdx.x * BX + threadIdx.x, y = blockIdx.y * BY + threadIdx.y;
+  if (x >= ei || y >= ej) return false;
+  i = i0 + x;
+  j = j0 + y;
+  k = k0 + (int)blockIdx.z;
+  return true;
+}
+
+__device__ __forceinline__ bool advanced(const Dims& d, int i, int j) {
+  return d.topo != JZ_TOPO_JET || (i >= 1 && i <= d.ni - 2 && j >= 1 && j <= d.nj - 2);
+}
+
+// Constants as pairs (hi, lo) of their FP64 values: an FP32 constant such as 0.4 would put an
+// error of ~1e-8 into every product.
+struct ConstsDF {
+  dfl gamma, gm1, gm1_half, S_hat, kappa2, kappa4, C_s, k_lam, k_sgs;
+  dfl mu_sut;        // mu_ref (1 + S_hat)
+  dfl third;         // 1/3
+  int sigma_is_two_thirds;
+  double sigma;
+};
+
+__device__ __forceinline__ dfl ld(const double* a, long long p) { return df_load(reinterpret_cast<const float2*>(a), p); }
+__device__ __forceinline__ void st(double* a, long long p, dfl v) { df_store(reinterpret_cast<float2*>(a), p, v); }
+
+// Anisotropic spectral radius lambda_d + lambda_d^(1-sigma) (lambda_e^sigma + lambda_f^sigma).
+__device__ __forceinline__ void aniso_df(const ConstsDF& c, const dfl lam[3], dfl Lam[3]) {
+  dfl lo[3], hi[3];
+  if (c.sigma_is_two_thirds) {
+    for (int d = 0; d < 3; ++d) df_cbrt_pair(lam[d], lo[d], hi[d]);
+  } else {
+    // a general exponent through FP64 pow (not on the benchmark path)
+    for (int d = 0; d < 3; ++d) {
+      const double l = df_to_f64(lam[d]);
+      lo[d] = df_of(l > 0.0 ? pow(l, 1.0 - c.sigma) : 0.0);
+      hi[d] = df_of(l > 0.0 ? pow(l, c.sigma) : 0.0);
+    }
+  }
+  Lam[0] = df_fma(lo[0], df_add(hi[1], hi[2]), lam[0]);
+  Lam[1] = df_fma(lo[1], df_add(hi[0], hi[2]), lam[1]);
+  Lam[2] = df_fma(lo[2], df_add(hi[0], hi[1]), lam[2]);
+}
+
+// A: every padded node.  Primitives, Sutherland mu, spectral radii and their anisotropic
+// scaling, transformed inviscid fluxes; the double-float copy of Q for the faces pass; at
+// stage 1 also the CFL rate of Q^n (block max, one atomic per block).
+__global__ void __launch_bounds__(BX* BY) k_nodal_df(Dims d, ConstsDF c, DFMetrics M, Work64 w, State q,
+                                                     QDF qdf, double* rate_max) {
+  int i, j, k;
+  double rate = 0.0;
+  if (node3(-kG, -kG, -kG, d.ni + 2 * kG, d.nj + 2 * kG, i, j, k)) {
+    const long long p = pidx(d, i, j, k);
+    const dfl rho = df_of(q.q[0][p]), m1 = df_of(q.q[1][p]), m2 = df_of(q.q[2][p]), m3 = df_of(q.q[3][p]),
+              e = df_of(q.q[4][p]);
+    st(qdf.q[0], p, rho); st(qdf.q[1], p, m1); st(qdf.q[2], p, m2); st(qdf.q[3], p, m3); st(qdf.q[4], p, e);
+    const dfl ir = df_rcp(rho);
+    const dfl u = df_mul(m1, ir), v = df_mul(m2, ir), ww = df_mul(m3, ir);
+    const dfl ke = df_fma(m3, ww, df_fma(m2, v, df_mul(m1, u)));            // rho |u|^2
+    const dfl pr = df_sub(df_mul(e, c.gm1), df_mul(ke, c.gm1_half));    // (gamma-1)(e - rho|u|^2/2)
+    const dfl T = df_mul(df_mul(pr, c.gamma), ir);
+    const dfl a = df_sqrt(T);
+    // Sutherland, eq. (sutherland), with T_inf = 1
+    const dfl mu = df_mul(df_mul(c.mu_sut, df_mul(T, a)), df_rcp(df_add(T, c.S_hat)));
+    st(w.u, p, u); st(w.v, p, v); st(w.w, p, ww); st(w.T, p, T); st(w.p, p, pr); st(w.mu, p, mu);
+    const dfl h0 = df_add(e, pr);
+    dfl lam[3];
+    for (int dir = 0; dir < 3; ++dir) {
+      const dfl sx = df_load(M.S[3 * dir], p), sy = df_load(M.S[3 * dir + 1], p), sz = df_load(M.S[3 * dir + 2], p);
+      const dfl U = df_fma(sz, ww, df_fma(sy, v, df_mul(sx, u)));
+      lam[dir] = df_fma(a, df_load(M.Smag[dir], p), df_abs(U));
+      st(w.H[dir][0], p, df_mul(rho, U));
+      st(w.H[dir][1], p, df_fma(m1, U, df_mul(pr, sx)));
+      st(w.H[dir][2], p, df_fma(m2, U, df_mul(pr, sy)));
+      st(w.H[dir][3], p, df_fma(m3, U, df_mul(pr, sz)));
+      st(w.H[dir][4], p, df_mul(h0, U));
+    }
+    if (rate_max && i >= 0 && i < d.ni && j >= 0 && j < d.nj && k >= 0 && k < d.nk && advanced(d, i, j))
+      rate = df_to_f64(df_mul(df_add(df_add(lam[0], lam[1]), lam[2]), df_load(M.invV, p)));
+    dfl Lam[3];
+    aniso_df(c, lam, Lam);
+    st(w.Lam[0], p, Lam[0]); st(w.Lam[1], p, Lam[1]); st(w.Lam[2], p, Lam[2]);
+  }
+  if (rate_max) {
+    // block max -> one atomic per block (non-negative doubles order like their bits)
+    __shared__ double redm[BX * BY / 32];
+    const int tid = threadIdx.y * BX + threadIdx.x;
+    for (int o = 16; o > 0; o >>= 1) rate = fmax(rate, __shfl_xor_sync(0xffffffffu, rate, o));
+    if ((tid & 31) == 0) redm[tid >> 5] = rate;
+    __syncthreads();
+    if (tid < 32) {
+      double x = tid < BX * BY / 32 ? redm[tid] : 0.0;
+      for (int o = 16; o > 0; o >>= 1) x = fmax(x, __shfl_xor_sync(0xffffffffu, x, o));
+      if (tid == 0 && x > 0.0)
+        atomicMax(reinterpret_cast<unsigned long long*>(rate_max), (unsigned long long)__double_as_longlong(x));
+    }
+  }
+}
+
+// B: nodes within one layer of the real region.  Gradients by the chain rule, strain rate,
+// Smagorinsky eddy viscosity, stresses and heat flux; H^dir -= S^dir_j F_j; pressure sensors.
+__global__ void __launch_bounds__(BX* BY) k_viscous_df(Dims d, ConstsDF c, DFMetrics M, Work64 w,
+                                                       const double* rho_df) {
+  int i, j, k;
+  if (!node3(-1, -1, -1, d.ni + 2, d.nj + 2, i, j, k)) return;
+  const long long p = pidx(d, i, j, k);
+  const long long s[3] = {1, d.sj, d.sk};
+  const double* f[4] = {w.u, w.v, w.w, w.T};
+  dfl S[3][3];
+  for (int dir = 0; dir < 3; ++dir)
+    for (int cc = 0; cc < 3; ++cc) S[dir][cc] = df_load(M.S[3 * dir + cc], p);
+  const dfl iV = df_load(M.invV, p);
+  // G[n][j] = sum_dir S^dir_j (f_n[+dir] - f_n[-dir]); the gradient is h G with h = 1/(2V)
+  dfl G[4][3];
+  for (int n = 0; n < 4; ++n) {
+    dfl dd[3];
+    for (int dir = 0; dir < 3; ++dir) dd[dir] = df_sub(ld(f[n], p + s[dir]), ld(f[n], p - s[dir]));
+    for (int jj = 0; jj < 3; ++jj) G[n][jj] = df_fma(S[2][jj], dd[2], df_fma(S[1][jj], dd[1], df_mul(S[0][jj], dd[0])));
+  }
+  const dfl h = df_scale(iV, 0.5f);
+  // |S| = h sqrt(2 sum G_ii^2 + sum_{i<j} A_ij^2), A_ij = G_ij + G_ji
+  const dfl A12 = df_add(G[0][1], G[1][0]), A13 = df_add(G[0][2], G[2][0]), A23 = df_add(G[1][2], G[2][1]);
+  const dfl Gd = df_add(df_add(G[0][0], G[1][1]), G[2][2]);
+  const dfl DG = df_fma(G[2][2], G[2][2], df_fma(G[1][1], G[1][1], df_mul(G[0][0], G[0][0])));
+  const dfl AA = df_fma(A23, A23, df_fma(A13, A13, df_mul(A12, A12)));
+  const dfl mu = ld(w.mu, p);
+  const dfl csd = df_mul(df_load(M.Delta, p), c.C_s);
+  // Smagorinsky eddy viscosity rho (C_s Delta)^2 |S|
+  const dfl mu_sgs = df_mul(df_mul(ld(rho_df, p), df_mul(csd, csd)), df_mul(h, df_sqrt(df_add(df_scale(DG, 2.f), AA))));
+  const dfl mt = df_add(mu, mu_sgs);
+  const dfl mV = df_mul(mt, iV), mh = df_mul(mt, h);
+  const dfl kh = df_mul(df_add(df_mul(mu, c.k_lam), df_mul(mu_sgs, c.k_sgs)), h);   // k_eff h
+  const dfl d3 = df_mul(Gd, c.third);                                                   // Gd / 3
+  const dfl t11 = df_mul(mV, df_sub(G[0][0], d3)), t22 = df_mul(mV, df_sub(G[1][1], d3)),
+            t33 = df_mul(mV, df_sub(G[2][2], d3));
+  const dfl t12 = df_mul(mh, A12), t13 = df_mul(mh, A13), t23 = df_mul(mh, A23);
+  const dfl tau[3][3] = {{t11, t12, t13}, {t12, t22, t23}, {t13, t23, t33}};
+  const dfl vel[3] = {ld(w.u, p), ld(w.v, p), ld(w.w, p)};
+  dfl F[3][4];
+  for (int jj = 0; jj < 3; ++jj) {
+    F[jj][0] = tau[0][jj];
+    F[jj][1] = tau[1][jj];
+    F[jj][2] = tau[2][jj];
+    F[jj][3] = df_fma(kh, G[3][jj], df_fma(vel[2], tau[2][jj], df_fma(vel[1], tau[1][jj], df_mul(vel[0], tau[0][jj]))));
+  }
+  for (int dir = 0; dir < 3; ++dir)
+    for (int m = 0; m < 4; ++m) {
+      const dfl sf = df_fma(S[dir][2], F[2][m], df_fma(S[dir][1], F[1][m], df_mul(S[dir][0], F[0][m])));
+      st(w.H[dir][m + 1], p, df_sub(ld(w.H[dir][m + 1], p), sf));
+    }
+  // pressure sensor along each direction: |p+ - 2p + p-| / (p+ + 2p + p-)
+  const dfl pc = ld(w.p, p);
+  const dfl pc2 = df_scale(pc, 2.f);
+  for (int dir = 0; dir < 3; ++dir) {
+    const dfl sum = df_add(ld(w.p, p + s[dir]), ld(w.p, p - s[dir]));
+    st(w.nu[dir], p, df_mul(df_abs(df_sub(sum, pc2)), df_rcp(df_add(sum, pc2))));
+  }
+}
+
+// C: faces n + 1/2 for n in [-1, n_dir - 1].  Turkel-Vatsa dissipation combined with the face
+// sum of H into the doubled total face flux G = H_n + H_(n+1) - 2 d_(n+1/2).
+__global__ void __launch_bounds__(BX* BY) k_faces_df(Dims d, ConstsDF c, Work64 w, QDF qdf) {
+  int i, j, k;
+  if (!node3(-1, -1, -1, d.ni + 1, d.nj + 1, i, j, k)) return;
+  const long long p = pidx(d, i, j, k);
+  const long long s[3] = {1, d.sj, d.sk};
+#pragma unroll
+  for (int dir = 0; dir < 3; ++dir) {
+    const long long sd = s[dir];
+    const dfl eps2 = df_mul(df_max(ld(w.nu[dir], p), ld(w.nu[dir], p + sd)), c.kappa2);
+    const dfl k4 = df_sub(c.kappa4, eps2);
+    const dfl eps4 = df_gt0(k4) ? k4 : df_make(0.f, 0.f);
+    // 2 d = a32 d1 - b2 e3 with Ls = 2 L_f, b2 = Ls eps4, a32 = 3 b2 + Ls eps2
+    const dfl Ls = df_add(ld(w.Lam[dir], p), ld(w.Lam[dir], p + sd));
+    const dfl b2 = df_mul(Ls, eps4);
+    const dfl a32 = df_fma(Ls, eps2, df_mul_f(b2, 3.f));
+#pragma unroll
+    for (int m = 0; m < 5; ++m) {
+      const double* Q = qdf.q[m];
+      const dfl d1 = df_sub(ld(Q, p + sd), ld(Q, p));
+      const dfl e3 = df_sub(ld(Q, p + 2 * sd), ld(Q, p - sd));
+      const dfl hs = df_add(ld(w.H[dir][m], p), ld(w.H[dir][m], p + sd));
+      st(w.G[dir][m], p, df_sub(df_fma(b2, e3, hs), df_mul(a32, d1)));
+    }
+  }
+}
+
+// D: real nodes.  2 V RHS = sum_dir (G(p) - G(p - s_dir)) in double-float; the stage
+// combination Q^n - alpha dt RHS in FP64 (mode 0) or the RHS itself (mode 1).
+template <int MODE>
+__global__ void __launch_bounds__(BX* BY) k_update_df(Dims d, GridDev g, Work64 w, State qin, State qn, State qout,
+                                                      const Scalars* sc, double alpha, int want_res, double* rhs_flat,
+                                                      double* res_sum) {
+  int i, j, k;
+  double r2 = 0.0;
+  if (node3(0, 0, 0, d.ni, d.nj, i, j, k)) {
+    const long long p = pidx(d, i, j, k);
+    const long long s[3] = {1, d.sj, d.sk};
+    const bool adv = advanced(d, i, j);
+    const double hV = 0.5 * g.invV[p];
+    double R[5];
+    for (int m = 0; m < 5; ++m) {
+      const dfl a = df_sub(ld(w.G[0][m], p), ld(w.G[0][m], p - s[0]));
+      const dfl b = df_sub(ld(w.G[1][m], p), ld(w.G[1][m], p - s[1]));
+      const dfl cc = df_sub(ld(w.G[2][m], p), ld(w.G[2][m], p - s[2]));
+      R[m] = df_to_f64(df_add(df_add(a, b), cc));
+    }
+    if (MODE == 0) {
+      const double adtV = alpha * sc->dt * hV;
+      for (int m = 0; m < 5; ++m) qout.q[m][p] = adv ? fma(-adtV, R[m], qn.q[m][p]) : qin.q[m][p];
+    } else {
+      const long long N = (long long)d.ni * d.nj * d.nk;
+      const long long t = ((long long)k * d.nj + j) * d.ni + i;
+      for (int m = 0; m < 5; ++m) rhs_flat[m * N + t] = adv ? R[m] * hV : 0.0;
+    }
+    if (adv) {
+      const double r0 = R[0] * hV;
+      r2 = r0 * r0;
+    }
+  }
+  if (want_res) {
+    __shared__ double red[BX * BY / 32];
+    const int tid = threadIdx.y * BX + threadIdx.x;
+    for (int o = 16; o > 0; o >>= 1) r2 += __shfl_xor_sync(0xffffffffu, r2, o);
+    if ((tid & 31) == 0) red[tid >> 5] = r2;
+    __syncthreads();
+    if (tid < 32) {
+      double x = tid < BX * BY / 32 ? red[tid] : 0.0;
+      for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+      if (tid == 0) atomicAdd(res_sum, x);
+    }
+  }
+}
+
+// FP64 metrics -> double-float copies (every padded node).
+__global__ void k_metrics_df(Dims d, GridDev g, DFMetrics M) {
+  const long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (p >= d.Np) return;
+  for (int c = 0; c < 9; ++c) df_store(M.S[c], p, df_of(g.S[c][p]));
+  for (int c = 0; c < 3; ++c) df_store(M.Smag[c], p, df_of(g.Smag[c][p]));
+  df_store(M.invV, p, df_of(g.invV[p]));
+  df_store(M.Delta, p, df_of(g.Delta[p]));
+}
+
+dfl pair_of(double x) {
+  const float h = (float)x;
+  return dfl{h, (float)(x - (double)h)};
+}
+
+ConstsDF make_cdf(const Consts& c) {
+  ConstsDF f;
+  f.gamma = pair_of(c.gamma);
+  f.gm1 = pair_of(c.gm1);
+  f.gm1_half = pair_of(c.gm1_half);
+  f.S_hat = pair_of(c.S_hat);
+  f.kappa2 = pair_of(c.kappa2);
+  f.kappa4 = pair_of(c.kappa4);
+  f.C_s = pair_of(c.C_s);
+  f.k_lam = pair_of(c.k_lam);
+  f.k_sgs = pair_of(c.k_sgs);
+  f.mu_sut = pair_of(c.mu_sut);
+  f.third = pair_of(1.0 / 3.0);
+  f.sigma_is_two_thirds = c.sigma_is_two_thirds;
+  f.sigma = c.sigma;
+  return f;
+}
+
+dim3 grid3(int ei, int ej, int ek) { return dim3((ei + BX - 1) / BX, (ej + BY - 1) / BY, ek); }
+
+}  // namespace
+
+cudaError_t metrics_to_df(const Dims& d, const GridDev& g, const DFMetrics& M, cudaStream_t st) {
+  k_metrics_df<<<blocks_for(d.Np, 256), 256, 0, st>>>(d, g, M);
+  return cudaGetLastError();
+}
+
+cudaError_t nodal_df(const Dims& d, const Consts& c, const DFMetrics& M, const Work64& w, const QDF& qdf,
+                     const State& qin, cudaStream_t st, double* rate_max) {
+  k_nodal_df<<<grid3(d.ni + 2 * kG, d.nj + 2 * kG, d.nk + 2 * kG), dim3(BX, BY), 0, st>>>(d, make_cdf(c), M, w, qin,
+                                                                                          qdf, rate_max);
+  return cudaGetLastError();
+}
+
+cudaError_t viscous_df(const Dims& d, const Consts& c, const DFMetrics& M, const Work64& w, const QDF& qdf,
+                       cudaStream_t st) {
+  k_viscous_df<<<grid3(d.ni + 2, d.nj + 2, d.nk + 2), dim3(BX, BY), 0, st>>>(d, make_cdf(c), M, w, qdf.q[0]);
+  return cudaGetLastError();
+}
+
+cudaError_t faces_df(const Dims& d, const Consts& c, const Work64& w, const QDF& qdf, cudaStream_t st) {
+  k_faces_df<<<grid3(d.ni + 1, d.nj + 1, d.nk + 1), dim3(BX, BY), 0, st>>>(d, make_cdf(c), w, qdf);
+  return cudaGetLastError();
+}
+
+cudaError_t update_df(const Dims& d, const GridDev& g, const Work64& w, const State& qin, const State& qn,
+                      const State& qout, const Scalars* sc, double alpha, int want_res, double* rhs_flat,
+                      cudaStream_t st) {
+  double* res_sum = const_cast<double*>(&sc->res_sum);
+  const dim3 gr = grid3(d.ni, d.nj, d.nk), blk(BX, BY);
+  if (rhs_flat)
+    k_update_df<1><<<gr, blk, 0, st>>>(d, g, w, qin, qn, qout, sc, alpha, 0, rhs_flat, res_sum);
+  else
+    k_update_df<0><<<gr, blk, 0, st>>>(d, g, w, qin, qn, qout, sc, alpha, want_res, nullptr, res_sum);
+  return cudaGetLastError();
+}
+
+}  // namespace jz

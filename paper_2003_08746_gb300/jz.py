@@ -20,7 +20,7 @@ LIB_PATH = os.path.join(HERE, "_build", "libjz.so")
 
 JZ_OK, JZ_ERR_ARG, JZ_ERR_CUDA, JZ_ERR_OOM, JZ_ERR_NONFINITE, JZ_ERR_STATE = 0, -1, -2, -3, -4, -5
 JZ_TOPO_PERIODIC, JZ_TOPO_JET = 1, 2
-JZ_PREC_FP64, JZ_PREC_FP32FLUX = 0, 1
+JZ_PREC_FP64, JZ_PREC_FP32FLUX, JZ_PREC_FP64PAIR = 0, 1, 2
 N_MODES, N_FREQ = 8, 4
 
 # Entry points declared in include/jz.h (checked by the tests).

@@ -35,21 +35,30 @@ def jz():
     return J
 
 
-def test_jet256x128x64_100_steps_fp64(jz):
-    """The 256 x 128 x 64 jet over its 100 RK steps (CFL time step, seeded entrance forcing):
-    state, time, last time step, last residual norm and totals against the oracle."""
+@pytest.fixture(scope="module")
+def jet256_ref():
+    """The oracle's 100 steps of the 256 x 128 x 64 jet (shared by the FP64 and pair forms)."""
     g, q, prm = W.make_workload("jet256x128x64")
+    og, oc = oracle_grid(g), O.Consts(prm)
+    ref, t, dts, R1 = O.run(og, torch.from_numpy(q), oc, 100)
+    return g, q, prm, og, ref, t, dts, R1
+
+
+@pytest.mark.parametrize("precision", ["fp64", "pair"])
+def test_jet256x128x64_100_steps_fp64(jz, jet256_ref, precision):
+    """The 256 x 128 x 64 jet over its 100 RK steps (CFL time step, seeded entrance forcing):
+    state, time, last time step, last residual norm and totals against the oracle, for the FP64
+    form and for its pair form (double-float stage arithmetic)."""
+    g, q, prm, og, ref, t, dts, R1 = jet256_ref
     grid = jz.Grid.from_workload(g)
-    s = jz.Solver(grid, prm)
+    s = jz.Solver(grid, prm, jz.JZ_PREC_FP64 if precision == "fp64" else jz.JZ_PREC_FP64PAIR)
     s.set_state(q, 0.0)
     st = s.step(100)
     got = s.get_state()
     s.close()
     grid.close()
-    og, oc = oracle_grid(g), O.Consts(prm)
-    ref, t, dts, R1 = O.run(og, torch.from_numpy(q), oc, 100)
     e2, em = field_errors(got, ref.numpy())
-    print(f"jet256x128x64 FP64 100 steps vs oracle: rel L2 {e2}, rel max {em}")
+    print(f"jet256x128x64 {precision} 100 steps vs oracle: rel L2 {e2}, rel max {em}")
     assert e2.max() <= TOL_L2, e2
     assert em.max() <= TOL_MAX, em
     assert abs(st.t - t.item()) <= 1e-13 * t.item()
@@ -116,7 +125,7 @@ def slab_refs(full_jet, slab_dt):
     return refs
 
 
-@pytest.mark.parametrize("precision", ["fp64", "fp32flux"])
+@pytest.mark.parametrize("precision", ["fp64", "pair", "fp32flux"])
 def test_jet1000x400x500_slabs_one_step(jz, full_jet, slab_dt, slab_refs, precision):
     """One RK step of the whole 1000 x 400 x 500 grid against the oracle's step of its first and
     last 40 i-planes: every node at least 14 planes from the slab's cut (the entrance, the axis,
@@ -125,8 +134,8 @@ def test_jet1000x400x500_slabs_one_step(jz, full_jet, slab_dt, slab_refs, precis
     the cut (metrics within 1 node, state within 2)."""
     g, q, _ = full_jet
     prm = W.jet_params(seed=2, dt_fixed=slab_dt)
-    prec = jz.JZ_PREC_FP64 if precision == "fp64" else jz.JZ_PREC_FP32FLUX
-    tol2, tolm, rtol = (TOL_L2, TOL_MAX, 1e-11) if precision == "fp64" else (1e-5, 1e-5, 2e-4)
+    prec = {"fp64": jz.JZ_PREC_FP64, "pair": jz.JZ_PREC_FP64PAIR, "fp32flux": jz.JZ_PREC_FP32FLUX}[precision]
+    tol2, tolm, rtol = (TOL_L2, TOL_MAX, 1e-11) if precision != "fp32flux" else (1e-5, 1e-5, 2e-4)
     grid = jz.Grid.from_workload(g)
     s = jz.Solver(grid, prm, prec)
     qd = torch.from_numpy(q).cuda()

@@ -198,17 +198,25 @@ def test_full_size_sampled_residual(jz, precision):
     grid.close()
 
 
-def test_jet_subsample_500_steps_fp64(jz):
-    """The 64 x 32 x 16 jet (the precision workload's subsample), 500 FP64 steps against the oracle."""
+@pytest.fixture(scope="module")
+def jet64_500_ref():
     g, q, prm = W.make_workload("jet64x32x16")
+    ref, _, _, _ = O.run(oracle_grid(g), torch.from_numpy(q), O.Consts(prm), 500)
+    return g, q, prm, ref.numpy()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "pair"])
+def test_jet_subsample_500_steps_fp64(jz, jet64_500_ref, precision):
+    """The 64 x 32 x 16 jet (the precision workload's subsample), 500 steps of the FP64 form and
+    of its pair form against the oracle."""
+    g, q, prm, ref = jet64_500_ref
     grid = jz.Grid.from_workload(g)
-    s = jz.Solver(grid, prm)
+    s = jz.Solver(grid, prm, jz.JZ_PREC_FP64 if precision == "fp64" else jz.JZ_PREC_FP64PAIR)
     s.set_state(q, 0.0)
     s.step(500, stats=False)
     got = s.get_state()
-    ref, _, _, _ = O.run(oracle_grid(g), torch.from_numpy(q), O.Consts(prm), 500)
-    e2, em = field_errors(got, ref.numpy())
-    print(f"jet64x32x16 FP64 500 steps vs oracle: rel L2 {e2}, rel max {em}")
+    e2, em = field_errors(got, ref)
+    print(f"jet64x32x16 {precision} 500 steps vs oracle: rel L2 {e2}, rel max {em}")
     assert e2.max() <= TOL_L2, e2
 
 
