@@ -49,6 +49,20 @@ FLOPS_PER_POINT = {"nodal": 83, "viscous": 227, "faces": 126, "update": 40}
 # dram__bytes_write.sum / nodes), scaled to the full launch by its node count;
 # profiles/k_viscous_fp64_jet256x128x64.md: (541.0 + 225.7) MB over 258 x 130 x 66 nodes.
 TRAFFIC_PER_NODE = {"viscous": 346.3}
+# FP32 instructions per node that the pair form's double-float arithmetic needs in each pass,
+# counted from the operations of jz_stagedf.cu with the cost of each operation in jz_df.cuh
+# (sum and difference 11, product 7, product by an FP32 number 5, fused multiply-add 15,
+# reciprocal 13, square root 12, cube-root pair 44, |x| 3, max 4; conversions and loads not
+# counted).  Nodal: 29 products, 20 fused multiply-adds, 6 sums, 2 reciprocals, 1 square root,
+# 3 |x|, 3 cube-root pairs = 748.  Viscous: 50 products, 61 fused multiply-adds, 44 sums and
+# differences, 1 square root, 3 reciprocals, 3 |x| = 1806.  Faces: 3 x (max 4, products 7 + 7,
+# differences 11 + 11, sum 11, fused multiply-add 15 + 5, select 2; and 5 x 66 per variable) =
+# 1176.  Update: 5 x 5 differences and sums = 275.
+PAIR_INST_PER_POINT = {"nodal": 748, "viscous": 1806, "faces": 1176, "update": 275}
+# DRAM bytes per node of a pair-form pass launch (dram__bytes_read.sum + dram__bytes_write.sum
+# over the launch's nodes), profiles/pair_passes_jet256x128x64.md.
+PAIR_TRAFFIC_PER_NODE = {"nodal": 345.1, "viscous": 347.9, "faces": 331.8, "update": 208.3}
+FP32_ISSUE_PEAK_TINST = 152 * 128 * 2.07e9 / 1e12      # 152 SMs x 4 x 32 lanes x 2.07 GHz
 # k_fused32: DRAM bytes per node averaged over a step's five launches (stage 1 and stage 2
 # captures in profiles/k_fused32_jet256x128x64.md); None until captured for the current kernel.
 TRAFFIC_FUSED32_PER_NODE = (129.5 + 4 * 174.7) / 5
@@ -434,9 +448,11 @@ def main():
         grid.close()
         return 0
 
-    # --- FP64 form (the method as defined; the headline) ---------------------
-    solver, r64 = timed_form(jz.JZ_PREC_FP64, True)
-    t_max, prof, clocks, stats = r64["ms"], r64["prof"], r64["clocks"], r64["stats"]
+    # --- FP64 form, pair arithmetic (the headline) ----------------------------
+    # FP64 state, stage combination and totals; fluxes, dissipation and SGS in double-float
+    # arithmetic on the FP32 pipes, held to the FP64 form's 1e-12 parity bar.
+    solver, rp = timed_form(jz.JZ_PREC_FP64PAIR, True)
+    t_max, prof, clocks, stats = rp["ms"], rp["prof"], rp["clocks"], rp["stats"]
     value = ws * npts * 5 * args.steps / (t_max / 1e3) / 1e9
 
     # end to end through the public API with pinned host buffers
@@ -453,18 +469,46 @@ def main():
     state_bytes = 5 * npts * 8
     solver.close()
 
-    # roofline of the dominant kernel (largest share of the timed region)
-    fp64_kinds = {k: v for k, v in prof.items() if k in FLOPS_PER_POINT and v[1] > 0}
-    top = max(fp64_kinds, key=lambda k: fp64_kinds[k][0])
-    top_ms, top_n = fp64_kinds[top]
+    # roofline of the dominant pass (largest share of the profiled pass): FP32 instructions that
+    # its double-float arithmetic needs per node (counted from the operations, PAIR_INST_PER_POINT)
+    # against the FP32 issue rate
+    pair_kinds = {k: v for k, v in prof.items() if k in PAIR_INST_PER_POINT and v[1] > 0}
+    top = max(pair_kinds, key=lambda k: pair_kinds[k][0])
+    top_ms, top_n = pair_kinds[top]
     pts = {"nodal": (g.ni + 4) * (g.nj + 4) * (g.nk + 4), "viscous": (g.ni + 2) * (g.nj + 2) * (g.nk + 2),
            "faces": (g.ni + 1) * (g.nj + 1) * (g.nk + 1), "update": npts}[top]
-    achieved = FLOPS_PER_POINT[top] * pts / (top_ms / top_n / 1e3) / 1e12
+    achieved = PAIR_INST_PER_POINT[top] * pts / (top_ms / top_n / 1e3) / 1e12
     total_prof = sum(v[0] for v in prof.values())
-    launches = int(sum(r64["launches"].values()))
+    launches = int(sum(rp["launches"].values()))
+    top_traffic = PAIR_TRAFFIC_PER_NODE.get(top)
+
+    # --- the same form with every operation in FP64 ------------------------------
+    variants = {}
+    solver64, r64 = timed_form(jz.JZ_PREC_FP64, False)
+    solver64.close()
+    v64 = ws * npts * 5 * args.steps / (r64["ms"] / 1e3) / 1e9
+    k64 = {k: v for k, v in r64["prof"].items() if k in FLOPS_PER_POINT and v[1] > 0}
+    top64 = max(k64, key=lambda k: k64[k][0])
+    pts64 = {"nodal": (g.ni + 4) * (g.nj + 4) * (g.nk + 4), "viscous": (g.ni + 2) * (g.nj + 2) * (g.nk + 2),
+             "faces": (g.ni + 1) * (g.nj + 1) * (g.nk + 1), "update": npts}[top64]
+    ach64 = FLOPS_PER_POINT[top64] * pts64 / (k64[top64][0] / k64[top64][1] / 1e3) / 1e12
+    tot64 = sum(v[0] for v in r64["prof"].values())
+    e2p, emp = field_errors(rp["final"].cpu().numpy(), r64["final"].cpu().numpy())
+    variants["fp64"] = {
+        "value": v64, "unit": "Gpoint-stage/s", "ms_per_step": r64["ms"] / args.steps, "dtype": "f64",
+        "roofline": {"bound": "alu", "kernel": top64, "achieved": ach64, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                     "frac": ach64 / FP64_PEAK_TFLOPS,
+                     "traffic": TRAFFIC_PER_NODE[top64] * pts64 if top64 in TRAFFIC_PER_NODE else None,
+                     "peak_source": "FP64 unit count x max SM clock (152 SMs x 4 flop/clk x 2.07 GHz)"},
+        "kernels": {k: {"ms_per_launch": v[0] / v[1], "launches": int(v[1]), "share": v[0] / tot64}
+                    for k, v in r64["prof"].items() if v[1] > 0},
+        "pair_form_rel_err": {"steps": args.warmup + args.steps + PROFILED_STEPS, "l2": e2p.tolist(),
+                              "max": emp.tolist(), "fields": ["rho", "rho_u", "rho_v", "rho_w", "e"]},
+        "pair_speedup": value / v64,
+    }
+    r64["final"] = rp["final"]        # the FP32-flux form is compared with the headline's state below
 
     # --- FP32-flux / FP64-state form ------------------------------------------
-    variants = {}
     if not args.no_fp32:
         solver32, r32 = timed_form(jz.JZ_PREC_FP32FLUX, False)
         # flow statistics: one sample = one HBM sweep (read rho, rho u_x, mean, M2; write mean, M2)
@@ -585,14 +629,16 @@ def main():
             "metric": "Gpoint-stage updates/s", "value": value, "unit": "Gpoint-stage/s",
             "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": t_max / args.steps, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "vs_baseline": None, "dtype": "f64 state and stage combination; f32-pair (double-float) flux arithmetic",
+            "data": "synthetic",
             "config": {"workload": args.workload, "points": npts, "dof": 5 * npts, "stages_per_step": 5,
-                       "precision": "fp64", "parallelism": f"replicas{ws}",
+                       "precision": "fp64pair", "parallelism": f"replicas{ws}",
                        "l2": "inputs larger than L2 (state 8 GB, metrics 16 GB per sweep)"},
-            "roofline": {"bound": "alu", "kernel": top, "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
-                         "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
-                         "traffic": TRAFFIC_PER_NODE[top] * pts if top in TRAFFIC_PER_NODE else None,
-                         "peak_source": "FP64 unit count x max SM clock (152 SMs x 4 flop/clk x 2.07 GHz)"},
+            "roofline": {"bound": "alu", "kernel": top, "achieved": achieved, "peak": FP32_ISSUE_PEAK_TINST,
+                         "unit": "T FP32-inst/s", "frac": achieved / FP32_ISSUE_PEAK_TINST,
+                         "traffic": top_traffic * pts if top_traffic else None,
+                         "algorithmic_fp32_inst_per_node": PAIR_INST_PER_POINT[top],
+                         "peak_source": "FP32 issue: 152 SMs x 128 lanes x 2.07 GHz"},
             "kernels": {k: {"ms_per_launch": v[0] / v[1], "launches": int(v[1]), "share": v[0] / total_prof}
                         for k, v in prof.items() if v[1] > 0},
             "kernels_from": f"profiled pass of {PROFILED_STEPS} steps right after the timed region (an event "
