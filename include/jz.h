@@ -62,8 +62,10 @@ extern "C" {
                                  its 1e-12 parity bar at FP32-pipe rates.
                                  Same memory as JZ_PREC_FP64 plus 152 bytes
                                  per padded node (metric and state copies).
-                                 jz_adjoint_step on such a solver runs the
-                                 FP64 passes.                                 */
+                                 jz_adjoint_step on such a solver advances
+                                 the states in pair arithmetic and runs the
+                                 transposed kernels (and the intermediates
+                                 they read) in FP64.                          */
 
 #define JZ_N_MODES 8          /* azimuthal forcing modes m = 0..7            */
 #define JZ_N_FREQ  4          /* forcing frequencies (Strouhal numbers)      */

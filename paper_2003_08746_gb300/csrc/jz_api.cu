@@ -371,13 +371,22 @@ int stats_sample(jz_solver* s) {
 }
 
 // ---- discrete adjoint: forward stages from an explicit Q^n --------------------------
+// A pair-form solver advances the states in pair arithmetic (the reverse sweep regenerates the
+// FP64 intermediates its transposed kernels read with the FP64 passes).
 int fwd_stage(jz_solver* s, const jz::State& in, const jz::State& qn, const jz::State& out, int l) {
   const jz::Dims& d = s->grid->d;
   const jz::GridDev& g = s->grid->g;
-  JZ_RUN(JZ_PROF_NODAL, jz::nodal64(d, s->c, g, s->w, in, s->st));
-  JZ_RUN(JZ_PROF_VISCOUS, jz::viscous64(d, s->c, g, s->w, in, s->st));
-  JZ_RUN(JZ_PROF_FACES, jz::faces64(d, s->c, s->w, in, s->st));
-  JZ_RUN(JZ_PROF_UPDATE, jz::update64(d, g, s->w, in, qn, out, s->sc, kAlpha[l], 0, nullptr, s->st));
+  if (s->pair) {
+    JZ_RUN(JZ_PROF_NODAL, jz::nodal_df(d, s->c, s->mdf, s->w, s->qdf, in, s->st));
+    JZ_RUN(JZ_PROF_VISCOUS, jz::viscous_df(d, s->c, s->mdf, s->w, s->qdf, s->st));
+    JZ_RUN(JZ_PROF_FACES, jz::faces_df(d, s->c, s->w, s->qdf, s->st));
+    JZ_RUN(JZ_PROF_UPDATE, jz::update_df(d, g, s->w, in, qn, out, s->sc, kAlpha[l], 0, nullptr, s->st));
+  } else {
+    JZ_RUN(JZ_PROF_NODAL, jz::nodal64(d, s->c, g, s->w, in, s->st));
+    JZ_RUN(JZ_PROF_VISCOUS, jz::viscous64(d, s->c, g, s->w, in, s->st));
+    JZ_RUN(JZ_PROF_FACES, jz::faces64(d, s->c, s->w, in, s->st));
+    JZ_RUN(JZ_PROF_UPDATE, jz::update64(d, g, s->w, in, qn, out, s->sc, kAlpha[l], 0, nullptr, s->st));
+  }
   if (d.topo == JZ_TOPO_JET) {
     JZ_RUN(JZ_PROF_BC, jz::bc_farfield(d, s->c, g, out, s->st));
     JZ_RUN(JZ_PROF_BC, jz::bc_inout(d, s->c, s->in, out, s->sc, kAlpha[l], s->st));

@@ -162,33 +162,39 @@ def test_jet1000x400x500_slabs_one_step(jz, full_jet, slab_dt, slab_refs, precis
     torch.cuda.empty_cache()
 
 
-def test_jet128x96x64_adjoint_vs_oracle_reverse_sweep(jz):
+@pytest.fixture(scope="module")
+def adj_ref():
+    """The oracle's reverse sweep on the 128 x 96 x 64 adjoint workload (10 steps, r = 0.75)."""
+    g, q, prm = W.make_workload("jet128x96x64", forcing_seed=4)
+    og, oc = oracle_grid(g), O.Consts(prm)
+    Q0 = torch.from_numpy(q)
+    dt = O.cfl_dt(og, Q0, oc).item()
+    obs = O.Observer(og, 0.75)
+    Jo, go = O.functional_gradient(og, Q0, oc, torch.as_tensor(np.asarray(prm.forcing_amp)), 10, dt, obs)
+    return g, q, prm, oc, dt, obs, Jo.item(), go.numpy()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "pair"])
+def test_jet128x96x64_adjoint_vs_oracle_reverse_sweep(jz, adj_ref, precision):
     """The 128 x 96 x 64 adjoint workload (forcing seed 4): J and dJ/dA of the observer
     functional at r = 0.75 over 10 steps, checkpoints every 5, against the oracle's reverse
     sweep; J within the error that the 1e-12 state bar allows (J is quadratic in a pressure
     fluctuation of ~1e-5, so its relative error is not bounded by 1e-12), the gradient to 1e-9
     of its largest component."""
-    g, q, prm = W.make_workload("jet128x96x64", forcing_seed=4)
+    g, q, prm, oc, dt, obs, Jo, go = adj_ref
     grid = jz.Grid.from_workload(g)
-    s = jz.Solver(grid, prm)
+    s = jz.Solver(grid, prm, jz.JZ_PREC_FP64 if precision == "fp64" else jz.JZ_PREC_FP64PAIR)
     s.set_state(q, 0.0)
-    A = np.asarray(prm.forcing_amp)
-    J, gr = jz.jz_adjoint_step(s.h, A, 10, 5, 0.75)
+    J, gr = jz.jz_adjoint_step(s.h, np.asarray(prm.forcing_amp), 10, 5, 0.75)
     s.close()
     grid.close()
-    og, oc = oracle_grid(g), O.Consts(prm)
-    Q0 = torch.from_numpy(q)
-    dt = O.cfl_dt(og, Q0, oc).item()
-    obs = O.Observer(og, 0.75)
-    Jo, go = O.functional_gradient(og, Q0, oc, torch.as_tensor(A), 10, dt, obs)
-    go = go.numpy()
     # J = sum_n dt sum_ik w_ik (p~ - p_inf)^2 is quadratic in a small fluctuation, so its error
     # follows from the state bar: a pressure error delta_p changes J by at most
     # 2 delta_p sum dt w |p~ - p_inf| <= 2 delta_p sqrt(Wt J) (Cauchy-Schwarz, Wt = sum_n dt sum_ik w_ik),
     # with delta_p = 1e-12 p_inf.
     Wt = 10 * dt * g.nk * float(obs.w.sum())
-    tol_J = 2.0 * TOL_L2 * oc.p_inf * np.sqrt(Wt * abs(Jo.item()))
-    print(f"jet128x96x64 adjoint 10 steps: J {J:.12e} vs {Jo.item():.12e} (bar {tol_J:.2e}), "
+    tol_J = 2.0 * TOL_L2 * oc.p_inf * np.sqrt(Wt * abs(Jo))
+    print(f"jet128x96x64 {precision} adjoint 10 steps: J {J:.12e} vs {Jo:.12e} (bar {tol_J:.2e}), "
           f"grad max err {np.abs(gr - go).max():.2e} of {np.abs(go).max():.2e}")
-    assert abs(J - Jo.item()) <= tol_J
+    assert abs(J - Jo) <= tol_J
     assert np.abs(gr - go).max() <= 1e-9 * np.abs(go).max()

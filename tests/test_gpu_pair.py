@@ -174,10 +174,9 @@ def test_pair_graph_replay_matches_plain_launches(jz):
     assert np.array_equal(out[0], out[1])
 
 
-def test_pair_adjoint_uses_fp64_passes(jz):
-    """jz_adjoint_step on a pair-form solver runs the FP64 passes: the same J and gradient as on
-    an FP64 solver (the gradient's sums are atomic, so their order, and the last bits, vary
-    from run to run)."""
+def test_pair_adjoint_matches_fp64_adjoint(jz):
+    """jz_adjoint_step on a pair-form solver (states advanced in pair arithmetic, transposed
+    kernels in FP64): J and the gradient within 1e-12 of an FP64 solver's."""
     g = W.jet_grid(20, 16, 8)
     prm = W.jet_params(seed=4)
     q = W.jet_state(g)
@@ -188,5 +187,5 @@ def test_pair_adjoint_uses_fp64_passes(jz):
         s.set_state(q, 0.0)
         res.append(jz.jz_adjoint_step(s.h, np.asarray(prm.forcing_amp), 4, 2, 0.75))
         s.close()
-    assert res[0][0] == res[1][0]
+    assert abs(res[0][0] - res[1][0]) <= 1e-12 * abs(res[0][0])
     assert np.abs(res[0][1] - res[1][1]).max() <= 1e-12 * np.abs(res[0][1]).max()
