@@ -64,8 +64,8 @@ PAIR_INST_PER_POINT = {"nodal": 748, "viscous": 1806, "faces": 1176, "update": 2
 PAIR_TRAFFIC_PER_NODE = {"nodal": 345.1, "viscous": 347.9, "faces": 331.8, "update": 208.3}
 FP32_ISSUE_PEAK_TINST = 152 * 128 * 2.07e9 / 1e12      # 152 SMs x 4 x 32 lanes x 2.07 GHz
 # k_fused32: DRAM bytes per node averaged over a step's five launches (stage 1 and stage 2
-# captures in profiles/k_fused32_jet256x128x64.md); None until captured for the current kernel.
-TRAFFIC_FUSED32_PER_NODE = (129.5 + 4 * 174.7) / 5
+# captures of the TMA-fed kernel, profiles/k_fused32_tma_jet256x128x64.md: 179.1 and 180.9 B).
+TRAFFIC_FUSED32_PER_NODE = (179.1 + 4 * 180.9) / 5
 
 
 def _dist():
@@ -201,7 +201,8 @@ def run_configs_table(args, jz, W, torch):
         qd = torch.from_numpy(q).cuda()
         del q
         row = {"workload": name, "points": g.npts, "gpu_steps": steps}
-        for form, prec in (("fp64", jz.JZ_PREC_FP64), ("fp32flux", jz.JZ_PREC_FP32FLUX)):
+        for form, prec in (("fp64", jz.JZ_PREC_FP64), ("fp64pair", jz.JZ_PREC_FP64PAIR),
+                           ("fp32flux", jz.JZ_PREC_FP32FLUX)):
             stream = torch.cuda.Stream()
             s = jz.Solver(grid, prm, prec, stream=stream.cuda_stream)
             s.set_state(qd, 0.0)
@@ -213,7 +214,7 @@ def run_configs_table(args, jz, W, torch):
             torch.cuda.synchronize()
             ms = e0.elapsed_time(e1) / steps
             rate = g.npts * 5 / (ms / 1e3)
-            bytes_ps = 192 if form == "fp64" else 152
+            bytes_ps = 152 if form == "fp32flux" else 192
             row[form] = {"ms_per_step": ms, "gpoint_stage_per_s": rate / 1e9,
                          "hbm_frac_algorithmic": rate * bytes_ps / 1e9 / hbm}
             s.close()

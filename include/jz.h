@@ -295,6 +295,18 @@ int jz_potential_core(const double* axis, const double* x, int ni, double u_jet,
  * Synchronous (legacy default stream).  Errors: JZ_ERR_ARG (NULL), JZ_ERR_CUDA. */
 int jz_check_math(double* rcp_max_rel, double* cbrt_max_rel, double* sqrt_max_rel);
 
+/* ---- self-check of the bounded wait ------------------------------------ *
+ * The paper has no counterpart: the FP32-flux stage kernel waits for its TMA
+ * copies on mbarriers with a bounded number of polls, and if a wait runs out
+ * it stops requesting copies, sets an error flag that jz_rk_step reports as
+ * JZ_ERR_CUDA, and finishes (the context stays usable).  This call runs the
+ * same bounded wait on an mbarrier that nothing ever arrives at: *timed_out
+ * is 1 when the wait ran out and returned, and *milliseconds how long it
+ * took (from clock64 at the device's nominal clock).  Synchronous; uses the
+ * legacy default stream; allocates 16 bytes of device memory.
+ * Errors: JZ_ERR_ARG (NULL), JZ_ERR_OOM, JZ_ERR_CUDA. */
+int jz_check_wait(int* timed_out, double* milliseconds);
+
 /* ---- snapshots (checkpoint / restart) ------------------------------------ *
  * The paper restarts long runs from stored solution files (Algorithm 2
  * starts from an initial condition or a restart file; Sec. "Parallel I/O"

@@ -1275,6 +1275,28 @@ int jz_check_math(double* rcp_max_rel, double* cbrt_max_rel, double* sqrt_max_re
   return JZ_OK;
 }
 
+int jz_check_wait(int* timed_out, double* milliseconds) {
+  if (!timed_out || !milliseconds) return fail(JZ_ERR_ARG, "jz_check_wait: NULL argument");
+  void* buf = nullptr;
+  cudaError_t e = cudaMalloc(&buf, 16);
+  if (e != cudaSuccess) return fail(alloc_status(e), "jz_check_wait: %s", cudaGetErrorString(e));
+  int* dt = static_cast<int*>(buf);
+  long long* dc = reinterpret_cast<long long*>(static_cast<char*>(buf) + 8);
+  e = jz::wait_check(dt, dc, nullptr);
+  int h_t = 0;
+  long long h_c = 0;
+  if (e == cudaSuccess) e = cudaMemcpy(&h_t, dt, sizeof h_t, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(&h_c, dc, sizeof h_c, cudaMemcpyDeviceToHost);
+  int clk_khz = 0, dev = 0;
+  if (e == cudaSuccess) e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&clk_khz, cudaDevAttrClockRate, dev);
+  cudaFree(buf);
+  if (e != cudaSuccess) return fail(JZ_ERR_CUDA, "jz_check_wait: %s", cudaGetErrorString(e));
+  *timed_out = h_t;
+  *milliseconds = clk_khz > 0 ? (double)h_c / (double)clk_khz : 0.0;
+  return JZ_OK;
+}
+
 int jz_station_profile(const double* field, const double* x, int ni, int nj, double x0, double* out) {
   if (!field || !x || !out || ni < 2 || nj < 1) return fail(JZ_ERR_ARG, "jz_station_profile: bad argument");
   if (!(x0 >= x[0] && x0 <= x[ni - 1])) return fail(JZ_ERR_ARG, "jz_station_profile: x0 outside the axial range");

@@ -324,6 +324,8 @@ cudaError_t shadow_refresh(const Dims& d, const Consts& c, const State& q, int f
 // of 8-byte elements; returns cudaErrorInvalidValue if the encoder is unavailable or refuses.
 cudaError_t make_shadow_map(const Dims& d, float2* sh, void* tmap128);
 cudaError_t fused32_slots(int* slots);
+// self-check of the fused kernel's bounded mbarrier wait (jz_check_wait)
+cudaError_t wait_check(int* dev_timed_out, long long* dev_cycles, cudaStream_t st);
 int fused32_tile_x();
 int fused32_tile_y();
 // Pair form of the FP64 stage (jz_stagedf.cu): the four passes in double-float arithmetic,

@@ -199,10 +199,10 @@ __device__ __forceinline__ void request_plane(const Args& A, Smem& sm, int slot,
       "l"(reinterpret_cast<unsigned long long>(&A.tm)), "r"(x0), "r"(y0), "r"(k + kG), "r"(0), "r"(smem_u32(b))
       : "memory");
 }
-// Wait for a slot's mbarrier phase with a bounded number of polls; false if it never completed.
-constexpr int kWaitPolls = 1 << 20;
-__device__ __forceinline__ bool wait_slot(Smem& sm, int slot, unsigned parity) {
-  const unsigned b = smem_u32(&sm.bar[slot]);
+// Wait for an mbarrier phase with a bounded number of polls; false if it never completed.
+constexpr int kWaitPolls = 1 << 18;   // ~1 s on GB300 (each unanswered try_wait suspends a few microseconds)
+__device__ __forceinline__ bool wait_bar(unsigned long long* bar, unsigned parity) {
+  const unsigned b = smem_u32(bar);
   for (int it = 0; it < kWaitPolls; ++it) {
     unsigned ok;
     asm volatile(
@@ -214,6 +214,7 @@ __device__ __forceinline__ bool wait_slot(Smem& sm, int slot, unsigned parity) {
   }
   return false;
 }
+__device__ __forceinline__ bool wait_slot(Smem& sm, int slot, unsigned parity) { return wait_bar(&sm.bar[slot], parity); }
 
 // Plane k of the CTA starting at k0 - 2 uses ring slot ring(k) for the ((k - k0 + 2) / 4)-th time.
 __device__ __forceinline__ unsigned plane_parity(int k, int k0) { return (unsigned)((k - k0 + 2) >> 2) & 1u; }
@@ -679,6 +680,24 @@ __global__ void k_shadow(Dims d, ConstsF c, State q, int full) {
   for (int m = 0; m < NSH; ++m) q.sh[m * d.Np + p] = s[m];
 }
 
+// Self-check of the bounded wait: one warp initialises an mbarrier that nothing ever arrives at
+// and waits for it with the stage kernel's bounded poll; the wait must run out and return.
+__global__ void k_wait_check(int* timed_out, long long* cycles) {
+  __shared__ unsigned long long bar;
+  if (threadIdx.x == 0) {
+    bar_init(&bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  const long long t0 = clock64();
+  const bool ok = wait_bar(&bar, 0);
+  const long long t1 = clock64();
+  if (threadIdx.x == 0) {
+    *timed_out = ok ? 0 : 1;
+    *cycles = t1 - t0;
+  }
+}
+
 ConstsF make_constsf(const Consts& c) {
   ConstsF f;
   f.gamma = (float)c.gamma; f.gm1 = (float)c.gm1; f.mu_ref = (float)c.mu_ref; f.S_hat = (float)c.S_hat;
@@ -779,6 +798,11 @@ cudaError_t fused32(const Dims& d, const Consts& c, const float* Mf, const State
   A.want_rate = want_rate;
   dim3 grid((d.ni + TX - 1) / TX, (d.nj + TY - 1) / TY, (d.nk + A.kchunk - 1) / A.kchunk);
   k_fused32<<<grid, NT, kSmemBytes, st>>>(A);
+  return cudaGetLastError();
+}
+
+cudaError_t wait_check(int* dev_timed_out, long long* dev_cycles, cudaStream_t st) {
+  k_wait_check<<<1, 32, 0, st>>>(dev_timed_out, dev_cycles);
   return cudaGetLastError();
 }
 

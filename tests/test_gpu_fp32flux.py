@@ -136,3 +136,18 @@ def test_precision_variant_jet512_500_steps(jz):
     e2s, ems = field_errors(got, ref.numpy())
     print(f"jet64x32x16 500 steps FP32-flux vs oracle: rel L2 {e2s}, rel max {ems}")
     assert e2s.max() <= TOL_STATE, e2s
+
+
+def test_bounded_wait_runs_out_and_context_stays_usable(jz):
+    """The stage kernel's bounded mbarrier wait, run on a barrier that nothing arrives at, runs
+    out and returns (no hang, no trap); afterwards the context still steps a solver."""
+    timed_out, ms = jz.jz_check_wait()
+    print(f"bounded wait ran out after {ms:.1f} ms")
+    assert timed_out == 1
+    assert 0.0 < ms < 20000.0
+    g, q, prm = W.make_workload("box32x24x16")
+    grid = jz.Grid.from_workload(g)
+    s = jz.Solver(grid, prm, jz.JZ_PREC_FP32FLUX)
+    s.set_state(q, 0.0)
+    st = s.step(2)
+    assert np.isfinite(s.get_state()).all() and st.t > 0.0
