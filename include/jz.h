@@ -295,6 +295,18 @@ int jz_potential_core(const double* axis, const double* x, int ni, double u_jet,
  * Synchronous (legacy default stream).  Errors: JZ_ERR_ARG (NULL), JZ_ERR_CUDA. */
 int jz_check_math(double* rcp_max_rel, double* cbrt_max_rel, double* sqrt_max_rel);
 
+/* ---- self-check of the pair arithmetic ----------------------------------- *
+ * The paper has no counterpart: JZ_PREC_FP64PAIR computes in double-float
+ * (pairs of FP32).  This call evaluates its operations on 2^20 operand sets
+ * (magnitudes 2^-40 .. 2^41, both signs) against FP64 and returns the largest
+ * errors in max_rel9[9]: sum (relative to |x| + |y|), product, fused
+ * multiply-add (relative to |x y| + |z|), reciprocal, square root, cube-root
+ * pair, the FP64 -> pair -> FP64 round trip, and the square root and
+ * cube-root pair of arguments below 1e-30 (their FP32 fallbacks).
+ * Synchronous; legacy default stream; allocates 72 bytes.
+ * Errors: JZ_ERR_ARG (NULL), JZ_ERR_OOM, JZ_ERR_CUDA. */
+int jz_check_pair(double* max_rel9);
+
 /* ---- self-check of the bounded wait ------------------------------------ *
  * The paper has no counterpart: the FP32-flux stage kernel waits for its TMA
  * copies on mbarriers with a bounded number of polls, and if a wait runs out

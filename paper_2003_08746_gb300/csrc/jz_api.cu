@@ -1275,6 +1275,18 @@ int jz_check_math(double* rcp_max_rel, double* cbrt_max_rel, double* sqrt_max_re
   return JZ_OK;
 }
 
+int jz_check_pair(double* max_rel9) {
+  if (!max_rel9) return fail(JZ_ERR_ARG, "jz_check_pair: NULL argument");
+  double* d = nullptr;
+  cudaError_t e = cudaMalloc(&d, 9 * sizeof(double));
+  if (e != cudaSuccess) return fail(alloc_status(e), "jz_check_pair: %s", cudaGetErrorString(e));
+  e = jz::df_check(d, nullptr);
+  if (e == cudaSuccess) e = cudaMemcpy(max_rel9, d, 9 * sizeof(double), cudaMemcpyDeviceToHost);
+  cudaFree(d);
+  if (e != cudaSuccess) return fail(JZ_ERR_CUDA, "jz_check_pair: %s", cudaGetErrorString(e));
+  return JZ_OK;
+}
+
 int jz_check_wait(int* timed_out, double* milliseconds) {
   if (!timed_out || !milliseconds) return fail(JZ_ERR_ARG, "jz_check_wait: NULL argument");
   void* buf = nullptr;

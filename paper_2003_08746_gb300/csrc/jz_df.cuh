@@ -145,7 +145,8 @@ __device__ __forceinline__ dfl df_sqrt(dfl x) {
   const float r = __fadd_rn(__fsub_rn(__fsub_rn(x.hi, pp), pe), x.lo);
   return df_norm(s, __fmul_rn(__fmul_rn(0.5f, y), r));
 }
-// x^(1/3) and x^(2/3) for x >= 0: seed z ~ x^(-1/3) from lg2/ex2; with e = 1 - x z^3 (in
+// x^(1/3) and x^(2/3) for x >= 0: seed z ~ x^(-1/3) from lg2/ex2 and one FP32 Newton step; with
+// e = 1 - x z^3 (in
 // double-float), x^(-1/3) = z (1 - e)^(-1/3) ~ z (1 + u), u = e (1/3 + 2e/9), the product z u
 // kept exactly (two_prod); then x^(2/3) = x x^(-1/3) and x^(1/3) = x^(2/3) x^(-1/3).
 __device__ __forceinline__ void df_cbrt_pair(dfl x, dfl& c1, dfl& c2) {
@@ -160,7 +161,10 @@ __device__ __forceinline__ void df_cbrt_pair(dfl x, dfl& c1, dfl& c2) {
     c2 = dfl{t * t, 0.f};
     return;
   }
-  const float z = mufu_ex2(mufu_lg2(x.hi) * (-1.f / 3.f));
+  // MUFU seed (~2^-19 for large exponents), one FP32 Newton step to ~2^-23, so that the
+  // FP32-rounded correction u below stays ~2^-47 of the result
+  const float z0 = mufu_ex2(mufu_lg2(x.hi) * (-1.f / 3.f));
+  const float z = __fmaf_rn(z0 * (1.f / 3.f), __fmaf_rn(-x.hi * z0, z0 * z0, 1.f), z0);
   const dfl z2 = df_norm(__fmul_rn(z, z), __fmaf_rn(z, z, -__fmul_rn(z, z)));   // z^2 exactly
   const dfl xz3 = df_mul_f(df_mul(x, z2), z);
   const float e = __fsub_rn(__fsub_rn(1.f, xz3.hi), xz3.lo);

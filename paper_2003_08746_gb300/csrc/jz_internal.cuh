@@ -356,6 +356,8 @@ cudaError_t stats_with(const Dims& d, const Consts& c, const GridDev& g, const S
 cudaError_t check_volume(const Dims& d, const GridDev& g, int* bad, cudaStream_t st);
 // self-check of rcp64 / cbrt64 (jz_mathcheck.cu)
 cudaError_t math_check(double* dev_maxrel3, cudaStream_t st);
+// self-check of the double-float operations of the pair form (jz_mathcheck.cu)
+cudaError_t df_check(double* dev_maxrel9, cudaStream_t st);
 // flow statistics of the axial velocity (jz_stats.cu)
 cudaError_t flow_sample(const Dims& d, const State& q, double* mean, double* m2, long long n, cudaStream_t st);
 cudaError_t flow_final(const Dims& d, const double* mean, const double* m2, long long n, double* out_mean,

@@ -29,7 +29,7 @@ EXPORTS = ("jz_last_error", "jz_version", "jz_create_grid", "jz_destroy_grid", "
            "jz_rk_step", "jz_profile", "jz_profile_read", "jz_profile_name", "jz_residual_noalloc",
            "jz_adjoint_step", "jz_save_snapshot", "jz_load_snapshot", "jz_stats_begin", "jz_stats_sample",
            "jz_stats_read", "jz_stats_end", "jz_station_profile", "jz_potential_core", "jz_check_math",
-           "jz_grid_compact", "jz_check_wait")
+           "jz_grid_compact", "jz_check_wait", "jz_check_pair")
 JZ_NOALLOC_SCRATCH_BYTES = 64 * 1024 * 1024
 JZ_NPROF = 10
 
@@ -93,6 +93,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
         "jz_grid_compact": ([vp], i),
         "jz_check_math": ([ctypes.POINTER(ctypes.c_double)] * 3, i),
         "jz_check_wait": ([ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)], i),
+        "jz_check_pair": ([ctypes.POINTER(ctypes.c_double)], i),
         "jz_stats_begin": ([vp, i], i),
         "jz_stats_sample": ([vp], i),
         "jz_stats_read": ([vp, vp, vp, ctypes.POINTER(ctypes.c_longlong)], i),
@@ -216,6 +217,14 @@ def jz_check_math():
     a, b, c = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
     _check(load().jz_check_math(ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
     return a.value, b.value, c.value
+
+
+def jz_check_pair():
+    """Largest errors of the pair (double-float) operations against FP64 on the device:
+    {add, mul, fma, rcp, sqrt, cbrt, roundtrip, sqrt_tiny, cbrt_tiny}."""
+    out = (ctypes.c_double * 9)()
+    _check(load().jz_check_pair(out))
+    return dict(zip(("add", "mul", "fma", "rcp", "sqrt", "cbrt", "roundtrip", "sqrt_tiny", "cbrt_tiny"), list(out)))
 
 
 def jz_check_wait():

@@ -189,3 +189,17 @@ def test_pair_adjoint_matches_fp64_adjoint(jz):
         s.close()
     assert abs(res[0][0] - res[1][0]) <= 1e-12 * abs(res[0][0])
     assert np.abs(res[0][1] - res[1][1]).max() <= 1e-12 * np.abs(res[0][1]).max()
+
+
+def test_pair_arithmetic_against_fp64(jz):
+    """The double-float operations on 2^20 operand sets against FP64: every one within ~2^-44
+    (sums and fused multiply-adds relative to the operands' magnitudes), the round trip of an
+    FP64 value through a pair within 2^-46, and roots of arguments below 1e-30 (the FP32
+    fallbacks) within FP32 rounding."""
+    e = jz.jz_check_pair()
+    print("pair arithmetic max errors:", {k: f"{v:.2e}" for k, v in e.items()})
+    for k in ("add", "mul", "fma", "rcp", "sqrt", "cbrt"):
+        assert e[k] <= 2.0 ** -44, (k, e[k])
+    assert e["roundtrip"] <= 2.0 ** -46
+    # below 1e-30 the roots are the FP32 fallbacks: FP32 rounding of the argument and result
+    assert e["sqrt_tiny"] <= 2.0 ** -22 and e["cbrt_tiny"] <= 2.0 ** -21
