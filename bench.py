@@ -59,9 +59,29 @@ TRAFFIC_PER_NODE = {"viscous": 346.3}
 # differences 11 + 11, sum 11, fused multiply-add 15 + 5, select 2; and 5 x 66 per variable) =
 # 1176.  Update: 5 x 5 differences and sums = 275.
 PAIR_INST_PER_POINT = {"nodal": 748, "viscous": 1806, "faces": 1176, "update": 275}
-# DRAM bytes per node of a pair-form pass launch (dram__bytes_read.sum + dram__bytes_write.sum
+
+
+def pair_inst_per_launch(g, kind):
+    """Algorithmic FP32 instructions of one launch of a pair-form kernel: the nodal pass over the
+    padded box, the viscous pass over the real box and one layer, and the faces kernel over the
+    faces n + 1/2 (n = -1 .. n_dir - 1) plus the update of every real node, which it also does."""
+    if kind == "nodal":
+        return PAIR_INST_PER_POINT["nodal"] * (g.ni + 4) * (g.nj + 4) * (g.nk + 4)
+    if kind == "viscous":
+        return PAIR_INST_PER_POINT["viscous"] * (g.ni + 2) * (g.nj + 2) * (g.nk + 2)
+    return (PAIR_INST_PER_POINT["faces"] * (g.ni + 1) * (g.nj + 1) * (g.nk + 1)
+            + PAIR_INST_PER_POINT["update"] * g.ni * g.nj * g.nk)
+
+
+def pair_launch_nodes(g, kind):
+    """Nodes a pair-form kernel launch covers (the faces kernel: the real nodes it updates)."""
+    e = {"nodal": 4, "viscous": 2}.get(kind, 0)
+    return (g.ni + e) * (g.nj + e) * (g.nk + e)
+
+
+# DRAM bytes per node of a pair-form kernel launch (dram__bytes_read.sum + dram__bytes_write.sum
 # over the launch's nodes), profiles/pair_passes_jet256x128x64.md.
-PAIR_TRAFFIC_PER_NODE = {"nodal": 345.1, "viscous": 347.9, "faces": 331.8, "update": 208.3}
+PAIR_TRAFFIC_PER_NODE = {"nodal": 345.0, "viscous": 346.6, "faces": 382.7}
 FP32_ISSUE_PEAK_TINST = 152 * 128 * 2.07e9 / 1e12      # 152 SMs x 4 x 32 lanes x 2.07 GHz
 # k_fused32: DRAM bytes per node averaged over a step's five launches (stage 1 and stage 2
 # captures of the TMA-fed kernel, profiles/k_fused32_tma_jet256x128x64.md: 179.1 and 180.9 B).
@@ -473,12 +493,12 @@ def main():
     # roofline of the dominant pass (largest share of the profiled pass): FP32 instructions that
     # its double-float arithmetic needs per node (counted from the operations, PAIR_INST_PER_POINT)
     # against the FP32 issue rate
-    pair_kinds = {k: v for k, v in prof.items() if k in PAIR_INST_PER_POINT and v[1] > 0}
+    pair_kinds = {k: v for k, v in prof.items() if k in PAIR_TRAFFIC_PER_NODE and v[1] > 0}
     top = max(pair_kinds, key=lambda k: pair_kinds[k][0])
     top_ms, top_n = pair_kinds[top]
-    pts = {"nodal": (g.ni + 4) * (g.nj + 4) * (g.nk + 4), "viscous": (g.ni + 2) * (g.nj + 2) * (g.nk + 2),
-           "faces": (g.ni + 1) * (g.nj + 1) * (g.nk + 1), "update": npts}[top]
-    achieved = PAIR_INST_PER_POINT[top] * pts / (top_ms / top_n / 1e3) / 1e12
+    top_inst = pair_inst_per_launch(g, top)
+    top_nodes = pair_launch_nodes(g, top)
+    achieved = top_inst / (top_ms / top_n / 1e3) / 1e12
     total_prof = sum(v[0] for v in prof.values())
     launches = int(sum(rp["launches"].values()))
     top_traffic = PAIR_TRAFFIC_PER_NODE.get(top)
@@ -639,8 +659,8 @@ def main():
                        "l2": "inputs larger than L2 (state 8 GB, metrics 16 GB per sweep)"},
             "roofline": {"bound": "alu", "kernel": top, "achieved": achieved, "peak": FP32_ISSUE_PEAK_TINST,
                          "unit": "T FP32-inst/s", "frac": achieved / FP32_ISSUE_PEAK_TINST,
-                         "traffic": top_traffic * pts if top_traffic else None,
-                         "algorithmic_fp32_inst_per_node": PAIR_INST_PER_POINT[top],
+                         "traffic": top_traffic * top_nodes if top_traffic else None,
+                         "algorithmic_fp32_inst_per_node": top_inst / top_nodes,
                          "peak_source": "FP32 issue: 152 SMs x 128 lanes x 2.07 GHz"},
             "kernels": {k: {"ms_per_launch": v[0] / v[1], "launches": int(v[1]), "share": v[0] / total_prof}
                         for k, v in prof.items() if v[1] > 0},

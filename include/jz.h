@@ -218,7 +218,7 @@ int jz_adjoint_step(jz_solver* s, const double* forcing_amps, int nsteps, int ck
  * Kernel kinds of the stage (index of the arrays below). */
 #define JZ_PROF_NODAL    0   /* FP64 nodal pass: primitives, spectral radii, inviscid fluxes */
 #define JZ_PROF_VISCOUS  1   /* FP64 viscous pass: gradients, SGS, viscous fluxes, sensor   */
-#define JZ_PROF_FACES    2   /* FP64 dissipation face fluxes                               */
+#define JZ_PROF_FACES    2   /* dissipation face fluxes (pair form: with the RHS and update) */
 #define JZ_PROF_UPDATE   3   /* RHS assembly and stage update                              */
 #define JZ_PROF_BC       4   /* boundary-condition kernels                                 */
 #define JZ_PROF_GHOST    5   /* ghost-point fill                                           */

@@ -247,8 +247,8 @@ int run_stage64(jz_solver* s, const jz::State& in, const jz::State& out, double 
                                        cfl_first ? &s->sc->rate_max : nullptr));
     if (cfl_first) JZ_RUN(JZ_PROF_REDUCE, jz::set_dt(s->c, s->sc, 0, s->st));
     JZ_RUN(JZ_PROF_VISCOUS, jz::viscous_df(d, s->c, s->mdf, s->w, s->qdf, s->st));
-    JZ_RUN(JZ_PROF_FACES, jz::faces_df(d, s->c, s->w, s->qdf, s->st));
-    JZ_RUN(JZ_PROF_UPDATE, jz::update_df(d, g, s->w, in, s->qn, out, s->sc, alpha, want_res, rhs_flat, s->st));
+    JZ_RUN(JZ_PROF_FACES, jz::faces_update_df(d, s->c, g, s->w, s->qdf, in, s->qn, out, s->sc, alpha, want_res,
+                                              rhs_flat, s->st));
     return JZ_OK;
   }
   JZ_RUN(JZ_PROF_NODAL, jz::nodal64(d, s->c, g, s->w, in, s->st, cfl_first ? &s->sc->rate_max : nullptr));
@@ -379,8 +379,8 @@ int fwd_stage(jz_solver* s, const jz::State& in, const jz::State& qn, const jz::
   if (s->pair) {
     JZ_RUN(JZ_PROF_NODAL, jz::nodal_df(d, s->c, s->mdf, s->w, s->qdf, in, s->st));
     JZ_RUN(JZ_PROF_VISCOUS, jz::viscous_df(d, s->c, s->mdf, s->w, s->qdf, s->st));
-    JZ_RUN(JZ_PROF_FACES, jz::faces_df(d, s->c, s->w, s->qdf, s->st));
-    JZ_RUN(JZ_PROF_UPDATE, jz::update_df(d, g, s->w, in, qn, out, s->sc, kAlpha[l], 0, nullptr, s->st));
+    JZ_RUN(JZ_PROF_FACES, jz::faces_update_df(d, s->c, g, s->w, s->qdf, in, qn, out, s->sc, kAlpha[l], 0, nullptr,
+                                              s->st));
   } else {
     JZ_RUN(JZ_PROF_NODAL, jz::nodal64(d, s->c, g, s->w, in, s->st));
     JZ_RUN(JZ_PROF_VISCOUS, jz::viscous64(d, s->c, g, s->w, in, s->st));

@@ -335,10 +335,9 @@ cudaError_t nodal_df(const Dims& d, const Consts& c, const DFMetrics& M, const W
                      const State& qin, cudaStream_t st, double* rate_max = nullptr);
 cudaError_t viscous_df(const Dims& d, const Consts& c, const DFMetrics& M, const Work64& w, const QDF& qdf,
                        cudaStream_t st);
-cudaError_t faces_df(const Dims& d, const Consts& c, const Work64& w, const QDF& qdf, cudaStream_t st);
-cudaError_t update_df(const Dims& d, const GridDev& g, const Work64& w, const State& qin, const State& qn,
-                      const State& qout, const Scalars* sc, double alpha, int want_res, double* rhs_flat,
-                      cudaStream_t st);
+cudaError_t faces_update_df(const Dims& d, const Consts& c, const GridDev& g, const Work64& w, const QDF& qdf,
+                            const State& qin, const State& qn, const State& qout, const Scalars* sc, double alpha,
+                            int want_res, double* rhs_flat, cudaStream_t st);
 // boundary conditions (jet), in this order after every stage
 cudaError_t bc_farfield(const Dims& d, const Consts& c, const GridDev& g, const State& q, cudaStream_t st);
 cudaError_t bc_inout(const Dims& d, const Consts& c, const Inflow& in, const State& q, const Scalars* sc,

@@ -1,14 +1,16 @@
-// Pair form of the FP64 stage: the four passes of jz_stage64.cu (nodal, viscous, faces,
-// update; Algorithm 2's inviscid flux, dissipation, viscous flux, RHS and Update(Cons, alpha_l))
-// with every flux, dissipation and SGS operation in double-float arithmetic (jz_df.cuh: pairs
-// of FP32 numbers, ~48 significant bits) and the stage combination Q^n - alpha dt RHS in FP64.
-// The state stays FP64; the nodal pass reads it once and leaves a double-float copy for the
-// dissipation of the faces pass; the intermediate fields are double-float pairs (float2) in the
-// FP64 form's work arrays (same size); the metrics are a double-float copy made when the solver
-// is created.
+// Pair form of the FP64 stage: the work of the four passes of jz_stage64.cu (nodal, viscous,
+// faces, update; Algorithm 2's inviscid flux, dissipation, viscous flux, RHS and
+// Update(Cons, alpha_l)) in three kernels, with every flux, dissipation and SGS operation in
+// double-float arithmetic (jz_df.cuh: pairs of FP32 numbers, ~48 significant bits) and the stage
+// combination Q^n - alpha dt RHS in FP64.  The state stays FP64; the nodal pass reads it once and
+// leaves a double-float copy for the dissipation; the intermediate fields are double-float pairs
+// (float2) in the FP64 form's work arrays (same size); the metrics are a double-float copy made
+// when the solver is created.  The last kernel forms the face fluxes and sums them into the RHS
+// of each node without storing them, so the pair form's results are those of separate faces and
+// update passes bit for bit.
 //
-// The passes are launched on 3-D grids (64 x 4 threads per block along i and j, one block row
-// per k), so no pass divides a flat index.
+// The nodal and viscous passes are launched on 3-D grids (64 x 4 threads per block along i and j,
+// one block row per k), so no pass divides a flat index.
 #include "jz_df.cuh"
 #include "jz_internal.cuh"
 
@@ -179,77 +181,121 @@ __global__ void __launch_bounds__(BX* BY) k_viscous_df(Dims d, ConstsDF c, DFMet
   }
 }
 
-// C: faces n + 1/2 for n in [-1, n_dir - 1].  Turkel-Vatsa dissipation combined with the face
-// sum of H into the doubled total face flux G = H_n + H_(n+1) - 2 d_(n+1/2).
-__global__ void __launch_bounds__(BX* BY) k_faces_df(Dims d, ConstsDF c, Work64 w, QDF qdf) {
-  int i, j, k;
-  if (!node3(-1, -1, -1, d.ni + 1, d.nj + 1, i, j, k)) return;
-  const long long p = pidx(d, i, j, k);
-  const long long s[3] = {1, d.sj, d.sk};
+// C + D: Turkel-Vatsa dissipation combined with the face sum of H into the doubled total face
+// flux G = H_n + H_(n+1) - 2 d_(n+1/2), and, in the same kernel, 2 V RHS = sum_dir (G(p) -
+// G(p - s_dir)) in double-float with the stage combination Q^n - alpha dt RHS in FP64 (mode 0)
+// or the RHS itself (mode 1).  The face fluxes never leave the SM: a block of 32 x 8 threads
+// marches along k over a chunk of planes; the thread at (i, j) forms the three faces i + 1/2,
+// j + 1/2, k + 1/2 of its node, takes the face i - 1/2 from the lane below it (shuffle), the face
+// j - 1/2 from the row below it (shared memory) and the face k - 1/2 from its own previous plane.
+// Column 0 and row 0 of the block are that halo (31 x 7 nodes updated per block and plane).
+constexpr int FX = 32, FY = 8;
+
+template <int DIR>
+__device__ __forceinline__ void face_df(const ConstsDF& c, const Work64& w, const QDF& qdf, long long p,
+                                        long long sd, dfl G[5]) {
+  const dfl eps2 = df_mul(df_max(ld(w.nu[DIR], p), ld(w.nu[DIR], p + sd)), c.kappa2);
+  const dfl k4 = df_sub(c.kappa4, eps2);
+  const dfl eps4 = df_gt0(k4) ? k4 : df_make(0.f, 0.f);
+  // 2 d = a32 d1 - b2 e3 with Ls = 2 L_f, b2 = Ls eps4, a32 = 3 b2 + Ls eps2
+  const dfl Ls = df_add(ld(w.Lam[DIR], p), ld(w.Lam[DIR], p + sd));
+  const dfl b2 = df_mul(Ls, eps4);
+  const dfl a32 = df_fma(Ls, eps2, df_mul_f(b2, 3.f));
 #pragma unroll
-  for (int dir = 0; dir < 3; ++dir) {
-    const long long sd = s[dir];
-    const dfl eps2 = df_mul(df_max(ld(w.nu[dir], p), ld(w.nu[dir], p + sd)), c.kappa2);
-    const dfl k4 = df_sub(c.kappa4, eps2);
-    const dfl eps4 = df_gt0(k4) ? k4 : df_make(0.f, 0.f);
-    // 2 d = a32 d1 - b2 e3 with Ls = 2 L_f, b2 = Ls eps4, a32 = 3 b2 + Ls eps2
-    const dfl Ls = df_add(ld(w.Lam[dir], p), ld(w.Lam[dir], p + sd));
-    const dfl b2 = df_mul(Ls, eps4);
-    const dfl a32 = df_fma(Ls, eps2, df_mul_f(b2, 3.f));
-#pragma unroll
-    for (int m = 0; m < 5; ++m) {
-      const double* Q = qdf.q[m];
-      const dfl d1 = df_sub(ld(Q, p + sd), ld(Q, p));
-      const dfl e3 = df_sub(ld(Q, p + 2 * sd), ld(Q, p - sd));
-      const dfl hs = df_add(ld(w.H[dir][m], p), ld(w.H[dir][m], p + sd));
-      st(w.G[dir][m], p, df_sub(df_fma(b2, e3, hs), df_mul(a32, d1)));
-    }
+  for (int m = 0; m < 5; ++m) {
+    const double* Q = qdf.q[m];
+    const dfl d1 = df_sub(ld(Q, p + sd), ld(Q, p));
+    const dfl e3 = df_sub(ld(Q, p + 2 * sd), ld(Q, p - sd));
+    const dfl hs = df_add(ld(w.H[DIR][m], p), ld(w.H[DIR][m], p + sd));
+    G[m] = df_sub(df_fma(b2, e3, hs), df_mul(a32, d1));
   }
 }
 
-// D: real nodes.  2 V RHS = sum_dir (G(p) - G(p - s_dir)) in double-float; the stage
-// combination Q^n - alpha dt RHS in FP64 (mode 0) or the RHS itself (mode 1).
+// Five blocks per SM (48 registers, a few spilled): 19.9 against 20.1 ms per launch at four
+// (64 registers) and 31.9 at three (80 registers, the face fluxes of the three directions held
+// in registers across the barrier) on 1000 x 400 x 500.
 template <int MODE>
-__global__ void __launch_bounds__(BX* BY) k_update_df(Dims d, GridDev g, Work64 w, State qin, State qn, State qout,
-                                                      const Scalars* sc, double alpha, int want_res, double* rhs_flat,
-                                                      double* res_sum) {
-  int i, j, k;
+__global__ void __launch_bounds__(FX* FY, 5) k_faces_update_df(Dims d, ConstsDF c, Work64 w, QDF qdf, const double* invV,
+                                                            State qin, State qn, State qout, const Scalars* sc,
+                                                            double alpha, int want_res, double* rhs_flat,
+                                                            double* res_sum, int kchunk) {
+  __shared__ float2 g1s[2][5][FY][FX];   // faces j + 1/2 of the plane, two planes in turn
+  __shared__ float2 g2s[5][FY][FX];      // each thread's face k - 1/2
+  const int x = threadIdx.x, y = threadIdx.y;
+  const int i = (int)blockIdx.x * (FX - 1) - 1 + x, j = (int)blockIdx.y * (FY - 1) - 1 + y;
+  const int k0 = (int)blockIdx.z * kchunk, k1 = min(k0 + kchunk, d.nk);
+  const bool inside = i <= d.ni - 1 && j <= d.nj - 1;     // i, j >= -1 by construction
+  const bool need0 = inside && y > 0;                      // face i + 1/2: halo column and body
+  const bool need1 = inside && x > 0;                      // face j + 1/2: halo row and body
+  const bool node = need0 && x > 0;                        // a real node this block updates
+  const bool adv = advanced(d, i, j);
+  const long long N = (long long)d.ni * d.nj * d.nk;
   double r2 = 0.0;
-  if (node3(0, 0, 0, d.ni, d.nj, i, j, k)) {
+  if (node) {
+    dfl g[5];
+    face_df<2>(c, w, qdf, pidx(d, i, j, k0 - 1), d.sk, g);
+#pragma unroll
+    for (int m = 0; m < 5; ++m) g2s[m][y][x] = make_float2(g[m].hi, g[m].lo);
+  }
+  for (int k = k0; k < k1; ++k) {
     const long long p = pidx(d, i, j, k);
-    const long long s[3] = {1, d.sj, d.sk};
-    const bool adv = advanced(d, i, j);
-    const double hV = 0.5 * g.invV[p];
-    double R[5];
+    const int b = k & 1;
+    dfl g[5] = {}, a[5], cc[5];
+    if (need0) face_df<0>(c, w, qdf, p, 1, g);
+#pragma unroll
     for (int m = 0; m < 5; ++m) {
-      const dfl a = df_sub(ld(w.G[0][m], p), ld(w.G[0][m], p - s[0]));
-      const dfl b = df_sub(ld(w.G[1][m], p), ld(w.G[1][m], p - s[1]));
-      const dfl cc = df_sub(ld(w.G[2][m], p), ld(w.G[2][m], p - s[2]));
-      R[m] = df_to_f64(df_add(df_add(a, b), cc));
+      const float lh = __shfl_up_sync(0xffffffffu, g[m].hi, 1), ll = __shfl_up_sync(0xffffffffu, g[m].lo, 1);
+      a[m] = df_sub(g[m], df_make(lh, ll));
     }
-    if (MODE == 0) {
-      const double adtV = alpha * sc->dt * hV;
-      for (int m = 0; m < 5; ++m) qout.q[m][p] = adv ? fma(-adtV, R[m], qn.q[m][p]) : qin.q[m][p];
-    } else {
-      const long long N = (long long)d.ni * d.nj * d.nk;
-      const long long t = ((long long)k * d.nj + j) * d.ni + i;
-      for (int m = 0; m < 5; ++m) rhs_flat[m * N + t] = adv ? R[m] * hV : 0.0;
+    if (need1) {
+      face_df<1>(c, w, qdf, p, d.sj, g);
+#pragma unroll
+      for (int m = 0; m < 5; ++m) g1s[b][m][y][x] = make_float2(g[m].hi, g[m].lo);
     }
-    if (adv) {
-      const double r0 = R[0] * hV;
-      r2 = r0 * r0;
+    if (node) {
+      face_df<2>(c, w, qdf, p, d.sk, g);
+#pragma unroll
+      for (int m = 0; m < 5; ++m) {
+        const float2 o = g2s[m][y][x];
+        cc[m] = df_sub(g[m], df_make(o.x, o.y));
+        g2s[m][y][x] = make_float2(g[m].hi, g[m].lo);
+      }
+    }
+    __syncthreads();
+    if (node) {
+      double R[5];
+#pragma unroll
+      for (int m = 0; m < 5; ++m) {
+        const float2 t1 = g1s[b][m][y][x], t0 = g1s[b][m][y - 1][x];
+        const dfl bb = df_sub(df_make(t1.x, t1.y), df_make(t0.x, t0.y));
+        R[m] = df_to_f64(df_add(df_add(a[m], bb), cc[m]));
+      }
+      const double hV = 0.5 * invV[p];
+      if (MODE == 0) {
+        const double adtV = alpha * sc->dt * hV;
+#pragma unroll
+        for (int m = 0; m < 5; ++m) qout.q[m][p] = adv ? fma(-adtV, R[m], qn.q[m][p]) : qin.q[m][p];
+      } else {
+        const long long t = ((long long)k * d.nj + j) * d.ni + i;
+#pragma unroll
+        for (int m = 0; m < 5; ++m) rhs_flat[m * N + t] = adv ? R[m] * hV : 0.0;
+      }
+      if (adv) {
+        const double r0 = R[0] * hV;
+        r2 += r0 * r0;
+      }
     }
   }
   if (want_res) {
-    __shared__ double red[BX * BY / 32];
-    const int tid = threadIdx.y * BX + threadIdx.x;
+    __shared__ double red[FX * FY / 32];
+    const int tid = y * FX + x;
     for (int o = 16; o > 0; o >>= 1) r2 += __shfl_xor_sync(0xffffffffu, r2, o);
     if ((tid & 31) == 0) red[tid >> 5] = r2;
     __syncthreads();
     if (tid < 32) {
-      double x = tid < BX * BY / 32 ? red[tid] : 0.0;
-      for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-      if (tid == 0) atomicAdd(res_sum, x);
+      double v = tid < FX * FY / 32 ? red[tid] : 0.0;
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (tid == 0) atomicAdd(res_sum, v);
     }
   }
 }
@@ -309,20 +355,27 @@ cudaError_t viscous_df(const Dims& d, const Consts& c, const DFMetrics& M, const
   return cudaGetLastError();
 }
 
-cudaError_t faces_df(const Dims& d, const Consts& c, const Work64& w, const QDF& qdf, cudaStream_t st) {
-  k_faces_df<<<grid3(d.ni + 1, d.nj + 1, d.nk + 1), dim3(BX, BY), 0, st>>>(d, make_cdf(c), w, qdf);
-  return cudaGetLastError();
+// planes per block of the faces-update kernel: enough blocks for several waves, one extra
+// k-face per chunk
+int faces_kchunk(const Dims& d) {
+  const long long tiles = (long long)((d.ni + FX - 2) / (FX - 1)) * ((d.nj + FY - 2) / (FY - 1));
+  int kc = 32;
+  while (kc > 4 && tiles * ((d.nk + kc - 1) / kc) < 8 * 152) kc /= 2;
+  return kc;
 }
 
-cudaError_t update_df(const Dims& d, const GridDev& g, const Work64& w, const State& qin, const State& qn,
-                      const State& qout, const Scalars* sc, double alpha, int want_res, double* rhs_flat,
-                      cudaStream_t st) {
+cudaError_t faces_update_df(const Dims& d, const Consts& c, const GridDev& g, const Work64& w, const QDF& qdf,
+                            const State& qin, const State& qn, const State& qout, const Scalars* sc, double alpha,
+                            int want_res, double* rhs_flat, cudaStream_t st) {
   double* res_sum = const_cast<double*>(&sc->res_sum);
-  const dim3 gr = grid3(d.ni, d.nj, d.nk), blk(BX, BY);
+  const int kc = faces_kchunk(d);
+  const dim3 gr((d.ni + FX - 2) / (FX - 1), (d.nj + FY - 2) / (FY - 1), (d.nk + kc - 1) / kc), blk(FX, FY);
+  const ConstsDF cdf = make_cdf(c);
   if (rhs_flat)
-    k_update_df<1><<<gr, blk, 0, st>>>(d, g, w, qin, qn, qout, sc, alpha, 0, rhs_flat, res_sum);
+    k_faces_update_df<1><<<gr, blk, 0, st>>>(d, cdf, w, qdf, g.invV, qin, qn, qout, sc, alpha, 0, rhs_flat, res_sum, kc);
   else
-    k_update_df<0><<<gr, blk, 0, st>>>(d, g, w, qin, qn, qout, sc, alpha, want_res, nullptr, res_sum);
+    k_faces_update_df<0><<<gr, blk, 0, st>>>(d, cdf, w, qdf, g.invV, qin, qn, qout, sc, alpha, want_res, nullptr,
+                                             res_sum, kc);
   return cudaGetLastError();
 }
 
