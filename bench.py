@@ -49,16 +49,17 @@ FLOPS_PER_POINT = {"nodal": 83, "viscous": 227, "faces": 126, "update": 40}
 # dram__bytes_write.sum / nodes), scaled to the full launch by its node count;
 # profiles/k_viscous_fp64_jet256x128x64.md: (541.0 + 225.7) MB over 258 x 130 x 66 nodes.
 TRAFFIC_PER_NODE = {"viscous": 346.3}
-# FP32 instructions per node that the pair form's double-float arithmetic needs in each pass,
+# FP32 instructions per node that the pair form's double-float arithmetic needs in each kernel,
 # counted from the operations of jz_stagedf.cu with the cost of each operation in jz_df.cuh
 # (sum and difference 11, product 7, product by an FP32 number 5, fused multiply-add 15,
-# reciprocal 13, square root 12, cube-root pair 44, |x| 3, max 4; conversions and loads not
-# counted).  Nodal: 29 products, 20 fused multiply-adds, 6 sums, 2 reciprocals, 1 square root,
-# 3 |x|, 3 cube-root pairs = 748.  Viscous: 50 products, 61 fused multiply-adds, 44 sums and
-# differences, 1 square root, 3 reciprocals, 3 |x| = 1806.  Faces: 3 x (max 4, products 7 + 7,
-# differences 11 + 11, sum 11, fused multiply-add 15 + 5, select 2; and 5 x 66 per variable) =
-# 1176.  Update: 5 x 5 differences and sums = 275.
-PAIR_INST_PER_POINT = {"nodal": 748, "viscous": 1806, "faces": 1176, "update": 275}
+# reciprocal 13, square root 12, cube-root pair 44, |x| 3, max 4, scaling by a power of two 2;
+# conversions and loads not counted).  Nodal: 14 products, 14 fused multiply-adds, 5 sums,
+# 2 reciprocals, 1 square root, 3 |x|, 3 cube-root pairs = 542.  Viscous: 64 products, 76 fused
+# multiply-adds, 45 sums and differences, 1 square root, 3 reciprocals, 3 |x|, 3 scalings = 2149
+# (the inviscid fluxes E^dir are formed here).  Faces: 3 x (max 4, products 7 + 7, difference 11,
+# sum 11, fused multiply-add 15, product by 3 5, select 2 = 62; and 5 x 66 per variable) = 1176.
+# Update: 5 x 5 differences and sums = 275.
+PAIR_INST_PER_POINT = {"nodal": 542, "viscous": 2149, "faces": 1176, "update": 275}
 
 
 def pair_inst_per_launch(g, kind):
@@ -81,7 +82,13 @@ def pair_launch_nodes(g, kind):
 
 # DRAM bytes per node of a pair-form kernel launch (dram__bytes_read.sum + dram__bytes_write.sum
 # over the launch's nodes), profiles/pair_passes_jet256x128x64.md.
-PAIR_TRAFFIC_PER_NODE = {"nodal": 345.0, "viscous": 346.6, "faces": 382.7}
+PAIR_TRAFFIC_PER_NODE = {"nodal": None, "viscous": None, "faces": 382.7}
+# Algorithmic DRAM bytes per node of each pair-form kernel (every field once, as double-float
+# pairs or FP64): nodal reads Q 40, S 72, |S| 24 and writes the pair copy of Q 40, u, v, w, T, p,
+# mu 48, Lambda 24 = 248; viscous reads S 72, 1/V 8, Delta 8, mu 8, u, v, w, T 32, p 8, the pair
+# copy of Q 40 and writes H 120, the sensors 24 = 320; faces-update reads the sensors 24, Lambda
+# 24, the pair copy of Q 40, H 120, Q^n 40, 1/V 8 and writes Q^(l) 40 = 296.
+PAIR_ALG_BYTES_PER_NODE = {"nodal": 248, "viscous": 320, "faces": 296}
 FP32_ISSUE_PEAK_TINST = 152 * 128 * 2.07e9 / 1e12      # 152 SMs x 4 x 32 lanes x 2.07 GHz
 # k_fused32: DRAM bytes per node averaged over a step's five launches (stage 1 and stage 2
 # captures of the TMA-fed kernel, profiles/k_fused32_tma_jet256x128x64.md: 179.1 and 180.9 B).
@@ -499,6 +506,7 @@ def main():
     top_inst = pair_inst_per_launch(g, top)
     top_nodes = pair_launch_nodes(g, top)
     achieved = top_inst / (top_ms / top_n / 1e3) / 1e12
+    top_gbs = PAIR_ALG_BYTES_PER_NODE[top] * top_nodes / (top_ms / top_n / 1e3) / 1e9
     total_prof = sum(v[0] for v in prof.values())
     launches = int(sum(rp["launches"].values()))
     top_traffic = PAIR_TRAFFIC_PER_NODE.get(top)
@@ -661,7 +669,9 @@ def main():
                          "unit": "T FP32-inst/s", "frac": achieved / FP32_ISSUE_PEAK_TINST,
                          "traffic": top_traffic * top_nodes if top_traffic else None,
                          "algorithmic_fp32_inst_per_node": top_inst / top_nodes,
-                         "peak_source": "FP32 issue: 152 SMs x 128 lanes x 2.07 GHz"},
+                         "peak_source": "FP32 issue: 152 SMs x 128 lanes x 2.07 GHz",
+                         "hbm": {"achieved_gbs": top_gbs, "frac": top_gbs / hbm_peak,
+                                 "algorithmic_bytes_per_node": PAIR_ALG_BYTES_PER_NODE[top]}},
             "kernels": {k: {"ms_per_launch": v[0] / v[1], "launches": int(v[1]), "share": v[0] / total_prof}
                         for k, v in prof.items() if v[1] > 0},
             "kernels_from": f"profiled pass of {PROFILED_STEPS} steps right after the timed region (an event "

@@ -65,8 +65,8 @@ __device__ __forceinline__ void aniso_df(const ConstsDF& c, const dfl lam[3], df
 }
 
 // A: every padded node.  Primitives, Sutherland mu, spectral radii and their anisotropic
-// scaling, transformed inviscid fluxes; the double-float copy of Q for the faces pass; at
-// stage 1 also the CFL rate of Q^n (block max, one atomic per block).
+// scaling; the double-float copy of Q for the viscous and faces passes; at stage 1 also the CFL
+// rate of Q^n (block max, one atomic per block).
 // Five blocks per SM (48 registers): the pass is bound by DRAM traffic and gains from the extra
 // warps (11.3 against 12.8 ms per launch on 1000 x 400 x 500); the viscous pass loses from the same.
 __global__ void __launch_bounds__(BX* BY, 5) k_nodal_df(Dims d, ConstsDF c, DFMetrics M, Work64 w, State q,
@@ -87,17 +87,11 @@ __global__ void __launch_bounds__(BX* BY, 5) k_nodal_df(Dims d, ConstsDF c, DFMe
     // Sutherland, eq. (sutherland), with T_inf = 1
     const dfl mu = df_mul(df_mul(c.mu_sut, df_mul(T, a)), df_rcp(df_add(T, c.S_hat)));
     st(w.u, p, u); st(w.v, p, v); st(w.w, p, ww); st(w.T, p, T); st(w.p, p, pr); st(w.mu, p, mu);
-    const dfl h0 = df_add(e, pr);
     dfl lam[3];
     for (int dir = 0; dir < 3; ++dir) {
       const dfl sx = df_load(M.S[3 * dir], p), sy = df_load(M.S[3 * dir + 1], p), sz = df_load(M.S[3 * dir + 2], p);
       const dfl U = df_fma(sz, ww, df_fma(sy, v, df_mul(sx, u)));
       lam[dir] = df_fma(a, df_load(M.Smag[dir], p), df_abs(U));
-      st(w.H[dir][0], p, df_mul(rho, U));
-      st(w.H[dir][1], p, df_fma(m1, U, df_mul(pr, sx)));
-      st(w.H[dir][2], p, df_fma(m2, U, df_mul(pr, sy)));
-      st(w.H[dir][3], p, df_fma(m3, U, df_mul(pr, sz)));
-      st(w.H[dir][4], p, df_mul(h0, U));
     }
     if (rate_max && i >= 0 && i < d.ni && j >= 0 && j < d.nj && k >= 0 && k < d.nk && advanced(d, i, j))
       rate = df_to_f64(df_mul(df_add(df_add(lam[0], lam[1]), lam[2]), df_load(M.invV, p)));
@@ -121,10 +115,14 @@ __global__ void __launch_bounds__(BX* BY, 5) k_nodal_df(Dims d, ConstsDF c, DFMe
   }
 }
 
-// B: nodes within one layer of the real region.  Gradients by the chain rule, strain rate,
-// Smagorinsky eddy viscosity, stresses and heat flux; H^dir -= S^dir_j F_j; pressure sensors.
-__global__ void __launch_bounds__(BX* BY) k_viscous_df(Dims d, ConstsDF c, DFMetrics M, Work64 w,
-                                                       const double* rho_df) {
+// B: nodes within one layer of the real region (the nodes whose fluxes the faces read).
+// Gradients by the chain rule, strain rate, Smagorinsky eddy viscosity, stresses and heat flux;
+// the transformed flux H^dir = E^dir - S^dir_j F_j, inviscid part E^dir from the nodal
+// primitives and the pair copy of Q, written once; pressure sensors.  Forming E^dir here rather
+// than in the nodal pass saves its store there and the load of it here (160 bytes per node):
+// 17.1 against 20.2 + 3.2 ms per launch on 1000 x 400 x 500.  Four blocks per SM (64 registers,
+// a few spilled): 17.1 against 17.6 ms at 80 registers.
+__global__ void __launch_bounds__(BX* BY, 4) k_viscous_df(Dims d, ConstsDF c, DFMetrics M, Work64 w, QDF qdf) {
   int i, j, k;
   if (!node3(-1, -1, -1, d.ni + 2, d.nj + 2, i, j, k)) return;
   const long long p = pidx(d, i, j, k);
@@ -150,7 +148,8 @@ __global__ void __launch_bounds__(BX* BY) k_viscous_df(Dims d, ConstsDF c, DFMet
   const dfl mu = ld(w.mu, p);
   const dfl csd = df_mul(df_load(M.Delta, p), c.C_s);
   // Smagorinsky eddy viscosity rho (C_s Delta)^2 |S|
-  const dfl mu_sgs = df_mul(df_mul(ld(rho_df, p), df_mul(csd, csd)), df_mul(h, df_sqrt(df_add(df_scale(DG, 2.f), AA))));
+  const dfl rho = ld(qdf.q[0], p);
+  const dfl mu_sgs = df_mul(df_mul(rho, df_mul(csd, csd)), df_mul(h, df_sqrt(df_add(df_scale(DG, 2.f), AA))));
   const dfl mt = df_add(mu, mu_sgs);
   const dfl mV = df_mul(mt, iV), mh = df_mul(mt, h);
   const dfl kh = df_mul(df_add(df_mul(mu, c.k_lam), df_mul(mu_sgs, c.k_sgs)), h);   // k_eff h
@@ -167,13 +166,22 @@ __global__ void __launch_bounds__(BX* BY) k_viscous_df(Dims d, ConstsDF c, DFMet
     F[jj][2] = tau[2][jj];
     F[jj][3] = df_fma(kh, G[3][jj], df_fma(vel[2], tau[2][jj], df_fma(vel[1], tau[1][jj], df_mul(vel[0], tau[0][jj]))));
   }
-  for (int dir = 0; dir < 3; ++dir)
+  const dfl pc = ld(w.p, p);
+  const dfl mq[3] = {ld(qdf.q[1], p), ld(qdf.q[2], p), ld(qdf.q[3], p)};
+  const dfl h0 = df_add(ld(qdf.q[4], p), pc);                                           // e + p
+  for (int dir = 0; dir < 3; ++dir) {
+    const dfl U = df_fma(S[dir][2], vel[2], df_fma(S[dir][1], vel[1], df_mul(S[dir][0], vel[0])));
+    dfl E[5];
+    E[0] = df_mul(rho, U);
+    for (int jj = 0; jj < 3; ++jj) E[jj + 1] = df_fma(mq[jj], U, df_mul(pc, S[dir][jj]));
+    E[4] = df_mul(h0, U);
+    st(w.H[dir][0], p, E[0]);
     for (int m = 0; m < 4; ++m) {
       const dfl sf = df_fma(S[dir][2], F[2][m], df_fma(S[dir][1], F[1][m], df_mul(S[dir][0], F[0][m])));
-      st(w.H[dir][m + 1], p, df_sub(ld(w.H[dir][m + 1], p), sf));
+      st(w.H[dir][m + 1], p, df_sub(E[m + 1], sf));
     }
+  }
   // pressure sensor along each direction: |p+ - 2p + p-| / (p+ + 2p + p-)
-  const dfl pc = ld(w.p, p);
   const dfl pc2 = df_scale(pc, 2.f);
   for (int dir = 0; dir < 3; ++dir) {
     const dfl sum = df_add(ld(w.p, p + s[dir]), ld(w.p, p - s[dir]));
@@ -351,7 +359,7 @@ cudaError_t nodal_df(const Dims& d, const Consts& c, const DFMetrics& M, const W
 
 cudaError_t viscous_df(const Dims& d, const Consts& c, const DFMetrics& M, const Work64& w, const QDF& qdf,
                        cudaStream_t st) {
-  k_viscous_df<<<grid3(d.ni + 2, d.nj + 2, d.nk + 2), dim3(BX, BY), 0, st>>>(d, make_cdf(c), M, w, qdf.q[0]);
+  k_viscous_df<<<grid3(d.ni + 2, d.nj + 2, d.nk + 2), dim3(BX, BY), 0, st>>>(d, make_cdf(c), M, w, qdf);
   return cudaGetLastError();
 }
 
