@@ -53,13 +53,15 @@ TRAFFIC_PER_NODE = {"viscous": 346.3}
 # counted from the operations of jz_stagedf.cu with the cost of each operation in jz_df.cuh
 # (sum and difference 11, product 7, product by an FP32 number 5, fused multiply-add 15,
 # reciprocal 13, square root 12, cube-root pair 44, |x| 3, max 4, scaling by a power of two 2;
+# in the viscous pass the unnormalized forms: sum 8, product 4, fused multiply-add 12, and 3 for
+# each of the 38 normalizations;
 # conversions and loads not counted).  Nodal: 14 products, 14 fused multiply-adds, 5 sums,
 # 2 reciprocals, 1 square root, 3 |x|, 3 cube-root pairs = 542.  Viscous: 64 products, 76 fused
-# multiply-adds, 45 sums and differences, 1 square root, 3 reciprocals, 3 |x|, 3 scalings = 2149
-# (the inviscid fluxes E^dir are formed here).  Faces: 3 x (max 4, products 7 + 7, difference 11,
+# multiply-adds, 45 sums and differences, 38 normalizations, 1 square root, 3 reciprocals, 3 |x|,
+# 3 scalings = 1708 (the inviscid fluxes E^dir are formed here).  Faces: 3 x (max 4, products 7 + 7, difference 11,
 # sum 11, fused multiply-add 15, product by 3 5, select 2 = 62; and 5 x 66 per variable) = 1176.
 # Update: 5 x 5 differences and sums = 275.
-PAIR_INST_PER_POINT = {"nodal": 542, "viscous": 2149, "faces": 1176, "update": 275}
+PAIR_INST_PER_POINT = {"nodal": 542, "viscous": 1708, "faces": 1176, "update": 275}
 
 
 def pair_inst_per_launch(g, kind):
@@ -82,7 +84,7 @@ def pair_launch_nodes(g, kind):
 
 # DRAM bytes per node of a pair-form kernel launch (dram__bytes_read.sum + dram__bytes_write.sum
 # over the launch's nodes), profiles/pair_passes_jet256x128x64.md.
-PAIR_TRAFFIC_PER_NODE = {"nodal": 229.7, "viscous": 313.8, "faces": 384.2}
+PAIR_TRAFFIC_PER_NODE = {"nodal": 229.7, "viscous": None, "faces": 384.2}
 # Algorithmic DRAM bytes per node of each pair-form kernel (every field once, as double-float
 # pairs or FP64): nodal reads Q 40, S 72, |S| 24 and writes the pair copy of Q 40, u, v, w, T, p,
 # mu 48, Lambda 24 = 248; viscous reads S 72, 1/V 8, Delta 8, mu 8, u, v, w, T 32, p 8, the pair

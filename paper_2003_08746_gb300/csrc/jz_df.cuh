@@ -93,6 +93,36 @@ __device__ __forceinline__ dfl df_fma(dfl x, dfl y, dfl z) {
   f = __fadd_rn(f, __fadd_rn(e, z.lo));
   return df_norm(s, f);
 }
+// Unnormalized ("lazy") forms of the sum, product and fused multiply-add: the same operations
+// without the final fast_two_sum.  That step is exact, so the value hi + lo is the one the
+// normalized form would give; only |lo| may exceed ulp(hi)/2 (by a few ulp).  A later operation
+// that takes such an input still carries lo through its error terms, at a cost of the same order
+// as its own rounding (~2^-46 relative).  A chain of them is normalized (df_n) before its value is
+// stored, compared, or seeds a reciprocal or root.
+__device__ __forceinline__ dfl df_add_l(dfl x, dfl y) {        // 8 operations
+  float s, e;
+  two_sum(x.hi, y.hi, s, e);
+  return dfl{s, __fadd_rn(e, __fadd_rn(x.lo, y.lo))};
+}
+__device__ __forceinline__ dfl df_sub_l(dfl x, dfl y) { return df_add_l(x, dfl{-y.hi, -y.lo}); }
+__device__ __forceinline__ dfl df_mul_l(dfl x, dfl y) {        // 4 operations
+  const float p = __fmul_rn(x.hi, y.hi);
+  float e = __fmaf_rn(x.hi, y.hi, -p);
+  e = __fmaf_rn(x.hi, y.lo, e);
+  e = __fmaf_rn(x.lo, y.hi, e);
+  return dfl{p, e};
+}
+__device__ __forceinline__ dfl df_fma_l(dfl x, dfl y, dfl z) {  // 12 operations
+  const float p = __fmul_rn(x.hi, y.hi);
+  float e = __fmaf_rn(x.hi, y.hi, -p);
+  e = __fmaf_rn(x.hi, y.lo, e);
+  e = __fmaf_rn(x.lo, y.hi, e);
+  float s, f;
+  two_sum(p, z.hi, s, f);
+  return dfl{s, __fadd_rn(f, __fadd_rn(e, z.lo))};
+}
+__device__ __forceinline__ dfl df_n(dfl x) { return df_norm(x.hi, x.lo); }
+
 // x * 2^k exactly (power-of-two scaling)
 __device__ __forceinline__ dfl df_scale(dfl x, float pow2) { return dfl{x.hi * pow2, x.lo * pow2}; }
 
