@@ -273,17 +273,18 @@ def run_configs_table(args, jz, W, torch):
     return 0
 
 
-def paper_mesh_row(jz, W, torch, name, steps, warmup, forms=("fp64", "fp32flux")):
+def paper_mesh_row(jz, W, torch, name, steps, warmup, forms=("fp64pair", "fp64", "fp32flux")):
     """Single-GPU throughput on one of the paper's Table "mesh" shapes (nk = 360 unique azimuthal
-    points): the FP64 form if its 600 bytes per padded node fit, then the FP32-flux form on the
-    full grid if that fits, else on a compact grid (FP32 metrics only, jz_grid_compact).  Grid
-    and state are built on the device; CUDA events on the solver's stream around `steps` steps
-    after `warmup` steps."""
+    points): the FP64 form in pair arithmetic and the all-FP64 form where their solvers (488 and
+    456 bytes per padded node beside the grid's 144) fit, then the FP32-flux form on the full grid
+    if that fits, else on a compact grid (FP32 metrics only, jz_grid_compact).  Grid and state are
+    built on the device; CUDA events on the solver's stream around `steps` steps after `warmup`
+    steps."""
     ni, nj = W.PAPER_MESHES[name]
     nk = 360
     npts = ni * nj * nk
     padded = ((ni + 4 + 3) // 4 * 4) * (nj + 4) * (nk + 4)
-    row = {"mesh": name, "shape": [ni, nj, nk], "points": npts, "fp64": None, "fp32flux": None}
+    row = {"mesh": name, "shape": [ni, nj, nk], "points": npts, "fp64pair": None, "fp64": None, "fp32flux": None}
     prm = W.jet_params(seed=2)
     free, _ = torch.cuda.mem_get_info()
     if (24 * npts + 144 * padded) > 0.9 * free or 216 * padded > 0.9 * free:
@@ -331,6 +332,10 @@ def paper_mesh_row(jz, W, torch, name, steps, warmup, forms=("fp64", "fp32flux")
         return {"ms_per_step": ms, "gpoint_stage_per_s": npts * 5 / (ms / 1e3) / 1e9, "min_p": st.min_p,
                 "steps": steps, "warmup": max(warmup, 1)}
 
+    free, _ = torch.cuda.mem_get_info()
+    if "fp64pair" in forms and 488 * padded + 40 * npts + 24 * npts < 0.9 * free:
+        row["fp64pair"] = timed(jz.JZ_PREC_FP64PAIR, 488 * padded)
+        row["fp64pair"]["grid"] = "full"
     free, _ = torch.cuda.mem_get_info()
     if "fp64" in forms and 456 * padded + 40 * npts + 24 * npts < 0.9 * free:
         row["fp64"] = timed(jz.JZ_PREC_FP64, 456 * padded)

@@ -60,8 +60,9 @@ extern "C" {
                                  arithmetic (pairs of FP32, ~48 bits) on the
                                  FP32 pipes: the FP64 form's results within
                                  its 1e-12 parity bar at FP32-pipe rates.
-                                 Same memory as JZ_PREC_FP64 plus 152 bytes
-                                 per padded node (metric and state copies).
+                                 488 bytes per padded node: 32 more than
+                                 JZ_PREC_FP64 (pair copies of the metrics
+                                 and state, 152; no stored face fluxes, -120).
                                  jz_adjoint_step on such a solver advances
                                  the states in pair arithmetic and runs the
                                  transposed kernels (and the intermediates

@@ -670,7 +670,9 @@ int jz_create(jz_grid* g, const jz_params* p, void* stream, jz_solver** out) {
       A(s->w.nu[dir], d.Np);
       for (int m = 0; m < 5; ++m) {
         A(s->w.H[dir][m], d.Np);
-        A(s->w.G[dir][m], d.Np);
+        // the face fluxes G of the FP64 faces and update passes; the pair form forms them on
+        // chip (and its adjoint regenerates only the nodal and viscous intermediates)
+        if (!s->pair) A(s->w.G[dir][m], d.Np);
       }
     }
   }
