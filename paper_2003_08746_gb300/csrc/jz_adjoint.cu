@@ -13,6 +13,7 @@
 // first argument on ties, |x| and sqrt(x) at 0 have derivative 0, cbrt'(0)
 // is 0, and the supersonic/subsonic and inflow/outflow switches take the
 // branch the forward pass took.
+#include "jz_df.cuh"
 #include "jz_internal.cuh"
 
 namespace jz {
@@ -29,6 +30,14 @@ __device__ __forceinline__ double nb(const Dims& d, const double* f, int i, int 
   int ii = i, jj = j, kk = k;
   if (dir == 0) ii += off; else if (dir == 1) jj += off; else kk += off;
   return in_box(d, ii, jj, kk) ? f[pidx(d, ii, jj, kk)] : 0.0;
+}
+
+// A forward intermediate (u, v, w, T, p, mu, the sensors, Lambda) at padded index p: FP64, or the
+// double-float pair the pair-form passes store in the same array, read back as hi + lo.
+template <bool PAIR>
+__device__ __forceinline__ double wv(const double* f, long long p) {
+  if (PAIR) return df_to_f64(df_load(reinterpret_cast<const float2*>(f), p));
+  return f[p];
 }
 
 __device__ __forceinline__ double sgn(double x) { return x > 0.0 ? 1.0 : (x < 0.0 ? -1.0 : 0.0); }
@@ -75,6 +84,7 @@ __global__ void k_adj_update(Dims d, GridDev g, Adj64 a, double adt) {
 }
 
 // ---- dissipation faces -------------------------------------------------------------
+template <bool PAIR>
 __global__ void k_adj_faces(Dims d, Consts c, Work64 w, State q, Adj64 a) {
   Box b{-1, -1, -1, d.ni + 1, d.nj + 1, d.nk + 1};
   int i, j, k;
@@ -83,12 +93,12 @@ __global__ void k_adj_faces(Dims d, Consts c, Work64 w, State q, Adj64 a) {
   const long long s[3] = {1, d.sj, d.sk};
   for (int dir = 0; dir < 3; ++dir) {
     const long long sd = s[dir];
-    const double nu0 = w.nu[dir][p], nu1 = w.nu[dir][p + sd];
+    const double nu0 = wv<PAIR>(w.nu[dir], p), nu1 = wv<PAIR>(w.nu[dir], p + sd);
     const bool first = nu0 >= nu1;
     const double eps2 = c.kappa2 * (first ? nu0 : nu1);
     const double k4 = c.kappa4 - eps2;
     const double eps4 = k4 > 0.0 ? k4 : 0.0;
-    const double Lf = 0.5 * (w.Lam[dir][p] + w.Lam[dir][p + sd]);
+    const double Lf = 0.5 * (wv<PAIR>(w.Lam[dir], p) + wv<PAIR>(w.Lam[dir], p + sd));
     double lf = 0.0, e2b = 0.0, e4b = 0.0;
     for (int m = 0; m < 5; ++m) {
       const double* Q = q.q[m];
@@ -111,6 +121,7 @@ __global__ void k_adj_faces(Dims d, Consts c, Work64 w, State q, Adj64 a) {
 }
 
 // ---- viscous pass and pressure sensor ----------------------------------------------
+template <bool PAIR>
 __global__ void k_adj_visc(Dims d, Consts c, GridDev g, Work64 w, State q, Adj64 a) {
   Box b{-1, -1, -1, d.ni + 2, d.nj + 2, d.nk + 2};
   int i, j, k;
@@ -131,7 +142,7 @@ __global__ void k_adj_visc(Dims d, Consts c, GridDev g, Work64 w, State q, Adj64
   double L[4][3];
   for (int n = 0; n < 4; ++n) {
     double dd[3];
-    for (int dir = 0; dir < 3; ++dir) dd[dir] = 0.5 * (f[n][p + s[dir]] - f[n][p - s[dir]]);
+    for (int dir = 0; dir < 3; ++dir) dd[dir] = 0.5 * (wv<PAIR>(f[n], p + s[dir]) - wv<PAIR>(f[n], p - s[dir]));
     for (int jj = 0; jj < 3; ++jj) L[n][jj] = iV * (S[0][jj] * dd[0] + S[1][jj] * dd[1] + S[2][jj] * dd[2]);
   }
   double Sij[3][3];
@@ -142,7 +153,7 @@ __global__ void k_adj_visc(Dims d, Consts c, GridDev g, Work64 w, State q, Adj64
   for (int x = 0; x < 3; ++x)
     for (int y = 0; y < 3; ++y) SS = SS + Sij[x][y] * Sij[x][y];
   const double Smod = sqrt64(2.0 * SS);
-  const double mu = w.mu[p];
+  const double mu = wv<PAIR>(w.mu, p);
   const double csd = c.C_s * g.Delta[p];
   const double rho = q.q[0][p];
   const double mu_sgs = rho * (csd * csd) * Smod;
@@ -152,7 +163,7 @@ __global__ void k_adj_visc(Dims d, Consts c, GridDev g, Work64 w, State q, Adj64
   double tau[3][3];
   for (int x = 0; x < 3; ++x)
     for (int y = 0; y < 3; ++y) tau[x][y] = 2.0 * mu_eff * (Sij[x][y] - (x == y ? d3 : 0.0));
-  const double vel[3] = {w.u[p], w.v[p], w.w[p]};
+  const double vel[3] = {wv<PAIR>(w.u, p), wv<PAIR>(w.v, p), wv<PAIR>(w.w, p)};
   // reverse: F^dir_m = S^dir_j F_j,m ; H = E - F
   double Fb[3][4];
   for (int jj = 0; jj < 3; ++jj)
@@ -195,10 +206,10 @@ __global__ void k_adj_visc(Dims d, Consts c, GridDev g, Work64 w, State q, Adj64
   a.mub[p] = mub;
   a.rhob[p] = rhob;
   // pressure sensor nu = |N|/Dn
-  const double pc = w.p[p];
+  const double pc = wv<PAIR>(w.p, p);
   for (int dir = 0; dir < 3; ++dir) {
     const double nub = a.nb0[dir][p] + a.nb1[dir][p - s[dir]];
-    const double pp = w.p[p + s[dir]], pm = w.p[p - s[dir]];
+    const double pp = wv<PAIR>(w.p, p + s[dir]), pm = wv<PAIR>(w.p, p - s[dir]);
     const double N = pp - 2.0 * pc + pm, Dn = pp + 2.0 * pc + pm;
     const double iD = rcp64(Dn);
     const double nu = fabs(N) * iD;
@@ -624,12 +635,17 @@ cudaError_t adj_update(const Dims& d, const GridDev& g, const Adj64& a, double a
 }
 
 cudaError_t adj_stage(const Dims& d, const Consts& c, const GridDev& g, const Work64& w, const State& q,
-                      const Adj64& a, cudaStream_t st) {
+                      const Adj64& a, int pair, cudaStream_t st) {
   const long long n0 = (long long)(d.ni + 2 * kG) * (d.nj + 2 * kG) * (d.nk + 2 * kG);
   const long long n1 = (long long)(d.ni + 2) * (d.nj + 2) * (d.nk + 2);
   const long long nf = (long long)(d.ni + 1) * (d.nj + 1) * (d.nk + 1);
-  k_adj_faces<<<blocks_for(nf, kTPB), kTPB, 0, st>>>(d, c, w, q, a);
-  k_adj_visc<<<blocks_for(n1, kTPB), kTPB, 0, st>>>(d, c, g, w, q, a);
+  if (pair) {
+    k_adj_faces<true><<<blocks_for(nf, kTPB), kTPB, 0, st>>>(d, c, w, q, a);
+    k_adj_visc<true><<<blocks_for(n1, kTPB), kTPB, 0, st>>>(d, c, g, w, q, a);
+  } else {
+    k_adj_faces<false><<<blocks_for(nf, kTPB), kTPB, 0, st>>>(d, c, w, q, a);
+    k_adj_visc<false><<<blocks_for(n1, kTPB), kTPB, 0, st>>>(d, c, g, w, q, a);
+  }
   k_adj_nodal<<<blocks_for(n0, kTPBN), kTPBN, 0, st>>>(d, c, g, w, q, a);
   const long long ei = d.ni + 2 * kG, ej = d.nj + 2 * kG;
   const long long ng = 4 * ei * ej + 4 * ei * d.nk + 4LL * d.nj * d.nk;

@@ -371,8 +371,8 @@ int stats_sample(jz_solver* s) {
 }
 
 // ---- discrete adjoint: forward stages from an explicit Q^n --------------------------
-// A pair-form solver advances the states in pair arithmetic (the reverse sweep regenerates the
-// FP64 intermediates its transposed kernels read with the FP64 passes).
+// A pair-form solver advances the states in pair arithmetic (its reverse sweep also regenerates
+// the intermediates the FP64 transposed kernels read with the pair nodal and viscous passes).
 int fwd_stage(jz_solver* s, const jz::State& in, const jz::State& qn, const jz::State& out, int l) {
   const jz::Dims& d = s->grid->d;
   const jz::GridDev& g = s->grid->g;
@@ -1006,9 +1006,15 @@ int jz_adjoint_step(jz_solver* s, const double* forcing_amps, int nsteps, int ck
       for (int l = 4; l >= 0; --l) {
         JZ_RUN(JZ_PROF_ADJOINT, jz::adj_bcs(d, s->c, g, s->in, *st[l + 1], a, tn + kAlpha[l] * dt, s->st));
         JZ_RUN(JZ_PROF_ADJOINT, jz::adj_update(d, g, a, kAlpha[l] * dt, s->st));
-        JZ_RUN(JZ_PROF_NODAL, jz::nodal64(d, s->c, g, s->w, *st[l], s->st));
-        JZ_RUN(JZ_PROF_VISCOUS, jz::viscous64(d, s->c, g, s->w, *st[l], s->st));
-        JZ_RUN(JZ_PROF_ADJOINT, jz::adj_stage(d, s->c, g, s->w, *st[l], a, s->st));
+        // the forward intermediates the transposed passes read, regenerated in the solver's form
+        if (s->pair) {
+          JZ_RUN(JZ_PROF_NODAL, jz::nodal_df(d, s->c, s->mdf, s->w, s->qdf, *st[l], s->st));
+          JZ_RUN(JZ_PROF_VISCOUS, jz::viscous_df(d, s->c, s->mdf, s->w, s->qdf, s->st));
+        } else {
+          JZ_RUN(JZ_PROF_NODAL, jz::nodal64(d, s->c, g, s->w, *st[l], s->st));
+          JZ_RUN(JZ_PROF_VISCOUS, jz::viscous64(d, s->c, g, s->w, *st[l], s->st));
+        }
+        JZ_RUN(JZ_PROF_ADJOINT, jz::adj_stage(d, s->c, g, s->w, *st[l], a, s->pair, s->st));
       }
       JZ_RUN(JZ_PROF_ADJOINT, jz::adj_add_qn(d, a, s->st));
     }

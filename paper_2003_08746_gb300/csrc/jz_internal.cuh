@@ -364,8 +364,9 @@ cudaError_t flow_final(const Dims& d, const double* mean, const double* m2, long
 
 // adjoint (jz_adjoint.cu)
 cudaError_t adj_update(const Dims& d, const GridDev& g, const Adj64& a, double adt, cudaStream_t st);
+// pair: the forward intermediates in w are the pair form's double-float pairs
 cudaError_t adj_stage(const Dims& d, const Consts& c, const GridDev& g, const Work64& w, const State& q,
-                      const Adj64& a, cudaStream_t st);
+                      const Adj64& a, int pair, cudaStream_t st);
 cudaError_t adj_add_qn(const Dims& d, const Adj64& a, cudaStream_t st);
 cudaError_t adj_bcs(const Dims& d, const Consts& c, const GridDev& g, const Inflow& in, const State& q,
                     const Adj64& a, double ts, cudaStream_t st);
