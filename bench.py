@@ -84,7 +84,7 @@ def pair_launch_nodes(g, kind):
 
 # DRAM bytes per node of a pair-form kernel launch (dram__bytes_read.sum + dram__bytes_write.sum
 # over the launch's nodes), profiles/pair_passes_jet256x128x64.md.
-PAIR_TRAFFIC_PER_NODE = {"nodal": 229.6, "viscous": 316.5, "faces": 383.3}
+PAIR_TRAFFIC_PER_NODE = {"nodal": 230.6, "viscous": 316.5, "faces": 338.4}
 # Algorithmic DRAM bytes per node of each pair-form kernel (every field once, as double-float
 # pairs or FP64): nodal reads Q 40, S 72, |S| 24 and writes the pair copy of Q 40, u, v, w, T, p,
 # mu 48, Lambda 24 = 248; viscous reads S 72, 1/V 8, Delta 8, mu 8, u, v, w, T 32, p 8, the pair

@@ -197,12 +197,12 @@ __global__ void __launch_bounds__(BX* BY, 4) k_viscous_df(Dims d, ConstsDF c, DF
 // C + D: Turkel-Vatsa dissipation combined with the face sum of H into the doubled total face
 // flux G = H_n + H_(n+1) - 2 d_(n+1/2), and, in the same kernel, 2 V RHS = sum_dir (G(p) -
 // G(p - s_dir)) in double-float with the stage combination Q^n - alpha dt RHS in FP64 (mode 0)
-// or the RHS itself (mode 1).  The face fluxes never leave the SM: a block of 32 x 8 threads
+// or the RHS itself (mode 1).  The face fluxes never leave the SM: a block of 32 x 16 threads
 // marches along k over a chunk of planes; the thread at (i, j) forms the three faces i + 1/2,
 // j + 1/2, k + 1/2 of its node, takes the face i - 1/2 from the lane below it (shuffle), the face
 // j - 1/2 from the row below it (shared memory) and the face k - 1/2 from its own previous plane.
-// Column 0 and row 0 of the block are that halo (31 x 7 nodes updated per block and plane).
-constexpr int FX = 32, FY = 8;
+// Column 0 and row 0 of the block are that halo (31 x 15 nodes updated per block and plane).
+constexpr int FX = 32, FY = 16;
 
 template <int DIR>
 __device__ __forceinline__ void face_df(const ConstsDF& c, const Work64& w, const QDF& qdf, long long p,
@@ -224,11 +224,13 @@ __device__ __forceinline__ void face_df(const ConstsDF& c, const Work64& w, cons
   }
 }
 
-// Five blocks per SM (48 registers, a few spilled): 19.9 against 20.1 ms per launch at four
-// (64 registers) and 31.9 at three (80 registers, the face fluxes of the three directions held
-// in registers across the barrier) on 1000 x 400 x 500.
+// Blocks of 32 x 16 threads, two per SM (64 registers): 19.2 ms per launch on 1000 x 400 x 500,
+// against 19.9 for 32 x 8 at five per SM (48 registers, a few spilled), 20.0 for 32 x 12 at
+// three, 21.3 for 32 x 4 at ten, 22.7 for 32 x 16 at three (40 registers) and 31.9 for 32 x 8
+// at three when the face fluxes of the three directions were held in registers across the
+// barrier (80 registers).
 template <int MODE>
-__global__ void __launch_bounds__(FX* FY, 5) k_faces_update_df(Dims d, ConstsDF c, Work64 w, QDF qdf, const double* invV,
+__global__ void __launch_bounds__(FX* FY, 2) k_faces_update_df(Dims d, ConstsDF c, Work64 w, QDF qdf, const double* invV,
                                                             State qin, State qn, State qout, const Scalars* sc,
                                                             double alpha, int want_res, double* rhs_flat,
                                                             double* res_sum, int kchunk) {
