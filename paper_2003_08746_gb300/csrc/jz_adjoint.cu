@@ -106,12 +106,14 @@ __global__ void k_adj_faces(Dims d, Consts c, Work64 w, State q, Adj64 a) {
       const double d1 = q1 - q0;
       const double d3 = q2 - 3.0 * q1 + 3.0 * q0 - qm;
       const double Db = a.acc[m][p + sd] - a.acc[m][p];
-      a.d1b[dir][m][p] = Db * Lf * eps2;
-      a.d3b[dir][m][p] = -Db * Lf * eps4;
       lf += Db * (eps2 * d1 - eps4 * d3);
       e2b += Db * Lf * d1;
       e4b += -Db * Lf * d3;
     }
+    // the face adjoints of d1 and d3 are Db Lf eps2 and -Db Lf eps4: the nodal gather forms them
+    // from these two coefficients and the differences of acc it reads anyway
+    a.ca2[dir][p] = Lf * eps2;
+    a.ca4[dir][p] = Lf * eps4;
     if (k4 > 0.0) e2b += -e4b;
     const double nub = c.kappa2 * e2b;
     a.nb0[dir][p] = first ? nub : 0.0;
@@ -244,14 +246,23 @@ __global__ void __launch_bounds__(kTPBN, 3) k_adj_nodal(Dims d, Consts c, GridDe
       Eb[dir][m] = 0.5 * (nb(d, a.acc[m], i, j, k, dir, -1) - nb(d, a.acc[m], i, j, k, dir, 1));
     Lamb[dir] = nb(d, a.lfh[dir], i, j, k, 0, 0) + nb(d, a.lfh[dir], i, j, k, dir, -1);
   }
-  double qb[5];
-  for (int m = 0; m < 5; ++m) {
-    double v = 0.0;
-    for (int dir = 0; dir < 3; ++dir)
-      v += nb(d, a.d3b[dir][m], i, j, k, dir, -2) + nb(d, a.d1b[dir][m], i, j, k, dir, -1) -
-           3.0 * nb(d, a.d3b[dir][m], i, j, k, dir, -1) - nb(d, a.d1b[dir][m], i, j, k, 0, 0) +
-           3.0 * nb(d, a.d3b[dir][m], i, j, k, 0, 0) - nb(d, a.d3b[dir][m], i, j, k, dir, 1);
-    qb[m] = v;
+  // dissipation: node n receives, from faces n-2 .. n+1 (f = face n + o), the adjoints of the
+  // differences it enters: d3(f-2) + d1(f-1) - 3 d3(f-1) - d1(f) + 3 d3(f) - d3(f+1), with
+  // d1(f) = Db(f) ca2(f), d3(f) = -Db(f) ca4(f), Db(f) = acc(f+1) - acc(f) (zero beyond the box)
+  double qb[5] = {0, 0, 0, 0, 0};
+  for (int dir = 0; dir < 3; ++dir) {
+    double c2[4], c4[4];           // faces n-2, n-1, n, n+1
+    for (int o = 0; o < 4; ++o) {
+      c2[o] = nb(d, a.ca2[dir], i, j, k, dir, o - 2);
+      c4[o] = nb(d, a.ca4[dir], i, j, k, dir, o - 2);
+    }
+    for (int m = 0; m < 5; ++m) {
+      const double am2 = nb(d, a.acc[m], i, j, k, dir, -2), am1 = nb(d, a.acc[m], i, j, k, dir, -1),
+                   a0 = nb(d, a.acc[m], i, j, k, 0, 0), ap1 = nb(d, a.acc[m], i, j, k, dir, 1),
+                   ap2 = nb(d, a.acc[m], i, j, k, dir, 2);
+      const double D0 = am1 - am2, D1 = a0 - am1, D2 = ap1 - a0, D3 = ap2 - ap1;
+      qb[m] += -D0 * c4[0] + D1 * c2[1] + 3.0 * (D1 * c4[1]) - D2 * c2[2] - 3.0 * (D2 * c4[2]) + D3 * c4[3];
+    }
   }
   qb[0] += nb(d, a.rhob, i, j, k, 0, 0);
   double mub = nb(d, a.mub, i, j, k, 0, 0);

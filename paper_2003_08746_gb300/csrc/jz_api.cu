@@ -900,9 +900,7 @@ int jz_adjoint_step(jz_solver* s, const double* forcing_amps, int nsteps, int ck
     A(a.lam[m], d.Np); A(a.qnbar[m], d.Np); A(a.acc[m], d.Np);
   }
   for (int dir = 0; dir < 3; ++dir) {
-    for (int m = 0; m < 5; ++m) {
-      A(a.d1b[dir][m], d.Np); A(a.d3b[dir][m], d.Np);
-    }
+    A(a.ca2[dir], d.Np); A(a.ca4[dir], d.Np);
     A(a.lfh[dir], d.Np); A(a.nb0[dir], d.Np); A(a.nb1[dir], d.Np);
     A(a.cpm[dir], d.Np); A(a.c0[dir], d.Np); A(a.ubd[dir], d.Np);
     for (int n = 0; n < 4; ++n) A(a.G[n][dir], d.Np);

@@ -258,8 +258,9 @@ struct Adj64 {
   double* lam[5];          // running adjoint of the stage state (real nodes; P0 as scratch)
   double* qnbar[5];        // adjoint of Q^n collected over the stages of a step
   double* acc[5];          // -(alpha dt / V) lam on advanced nodes, 0 elsewhere
-  double* d1b[3][5];       // face adjoints: d(out)/d(Q_{n+1} - Q_n)
-  double* d3b[3][5];       //               d(out)/d(third difference)
+  double* ca2[3];          // face coefficient Lambda_f eps2: the face adjoint of Q_{n+1} - Q_n
+                           // is (acc_{n+1} - acc_n) ca2, that of the third difference
+  double* ca4[3];          // -(acc_{n+1} - acc_n) ca4 with ca4 = Lambda_f eps4
   double* lfh[3];          // half the adjoint of the face spectral radius
   double* nb0[3];          // sensor adjoint sent to node n of face n+1/2
   double* nb1[3];          // ... and to node n+1
