@@ -64,9 +64,10 @@ extern "C" {
                                  JZ_PREC_FP64 (pair copies of the metrics
                                  and state, 152; no stored face fluxes, -120).
                                  jz_adjoint_step on such a solver advances
-                                 the states and regenerates the intermediates
-                                 in pair arithmetic and runs the transposed
-                                 kernels in FP64.                             */
+                                 the states, regenerates the intermediates and
+                                 runs the transposed viscous pass in pair
+                                 arithmetic, the other transposed passes in
+                                 FP64.                                        */
 
 #define JZ_N_MODES 8          /* azimuthal forcing modes m = 0..7            */
 #define JZ_N_FREQ  4          /* forcing frequencies (Strouhal numbers)      */

@@ -122,8 +122,7 @@ __global__ void k_adj_faces(Dims d, Consts c, Work64 w, State q, Adj64 a) {
   }
 }
 
-// ---- viscous pass and pressure sensor ----------------------------------------------
-template <bool PAIR>
+// ---- viscous pass and pressure sensor (FP64 solvers; pair solvers: k_adj_visc_df) ----
 __global__ void k_adj_visc(Dims d, Consts c, GridDev g, Work64 w, State q, Adj64 a) {
   Box b{-1, -1, -1, d.ni + 2, d.nj + 2, d.nk + 2};
   int i, j, k;
@@ -144,7 +143,7 @@ __global__ void k_adj_visc(Dims d, Consts c, GridDev g, Work64 w, State q, Adj64
   double L[4][3];
   for (int n = 0; n < 4; ++n) {
     double dd[3];
-    for (int dir = 0; dir < 3; ++dir) dd[dir] = 0.5 * (wv<PAIR>(f[n], p + s[dir]) - wv<PAIR>(f[n], p - s[dir]));
+    for (int dir = 0; dir < 3; ++dir) dd[dir] = 0.5 * (f[n][p + s[dir]] - f[n][p - s[dir]]);
     for (int jj = 0; jj < 3; ++jj) L[n][jj] = iV * (S[0][jj] * dd[0] + S[1][jj] * dd[1] + S[2][jj] * dd[2]);
   }
   double Sij[3][3];
@@ -155,7 +154,7 @@ __global__ void k_adj_visc(Dims d, Consts c, GridDev g, Work64 w, State q, Adj64
   for (int x = 0; x < 3; ++x)
     for (int y = 0; y < 3; ++y) SS = SS + Sij[x][y] * Sij[x][y];
   const double Smod = sqrt64(2.0 * SS);
-  const double mu = wv<PAIR>(w.mu, p);
+  const double mu = w.mu[p];
   const double csd = c.C_s * g.Delta[p];
   const double rho = q.q[0][p];
   const double mu_sgs = rho * (csd * csd) * Smod;
@@ -165,7 +164,7 @@ __global__ void k_adj_visc(Dims d, Consts c, GridDev g, Work64 w, State q, Adj64
   double tau[3][3];
   for (int x = 0; x < 3; ++x)
     for (int y = 0; y < 3; ++y) tau[x][y] = 2.0 * mu_eff * (Sij[x][y] - (x == y ? d3 : 0.0));
-  const double vel[3] = {wv<PAIR>(w.u, p), wv<PAIR>(w.v, p), wv<PAIR>(w.w, p)};
+  const double vel[3] = {w.u[p], w.v[p], w.w[p]};
   // reverse: F^dir_m = S^dir_j F_j,m ; H = E - F
   double Fb[3][4];
   for (int jj = 0; jj < 3; ++jj)
@@ -208,10 +207,10 @@ __global__ void k_adj_visc(Dims d, Consts c, GridDev g, Work64 w, State q, Adj64
   a.mub[p] = mub;
   a.rhob[p] = rhob;
   // pressure sensor nu = |N|/Dn
-  const double pc = wv<PAIR>(w.p, p);
+  const double pc = w.p[p];
   for (int dir = 0; dir < 3; ++dir) {
     const double nub = a.nb0[dir][p] + a.nb1[dir][p - s[dir]];
-    const double pp = wv<PAIR>(w.p, p + s[dir]), pm = wv<PAIR>(w.p, p - s[dir]);
+    const double pp = w.p[p + s[dir]], pm = w.p[p - s[dir]];
     const double N = pp - 2.0 * pc + pm, Dn = pp + 2.0 * pc + pm;
     const double iD = rcp64(Dn);
     const double nu = fabs(N) * iD;
@@ -646,16 +645,18 @@ cudaError_t adj_update(const Dims& d, const GridDev& g, const Adj64& a, double a
 }
 
 cudaError_t adj_stage(const Dims& d, const Consts& c, const GridDev& g, const Work64& w, const State& q,
-                      const Adj64& a, int pair, cudaStream_t st) {
+                      const Adj64& a, const DFMetrics* mdf, const QDF* qdf, cudaStream_t st) {
+  const bool pair = mdf && qdf;
   const long long n0 = (long long)(d.ni + 2 * kG) * (d.nj + 2 * kG) * (d.nk + 2 * kG);
   const long long n1 = (long long)(d.ni + 2) * (d.nj + 2) * (d.nk + 2);
   const long long nf = (long long)(d.ni + 1) * (d.nj + 1) * (d.nk + 1);
   if (pair) {
     k_adj_faces<true><<<blocks_for(nf, kTPB), kTPB, 0, st>>>(d, c, w, q, a);
-    k_adj_visc<true><<<blocks_for(n1, kTPB), kTPB, 0, st>>>(d, c, g, w, q, a);
+    const cudaError_t e = adj_visc_df(d, c, *mdf, w, *qdf, a, st);
+    if (e != cudaSuccess) return e;
   } else {
     k_adj_faces<false><<<blocks_for(nf, kTPB), kTPB, 0, st>>>(d, c, w, q, a);
-    k_adj_visc<false><<<blocks_for(n1, kTPB), kTPB, 0, st>>>(d, c, g, w, q, a);
+    k_adj_visc<<<blocks_for(n1, kTPB), kTPB, 0, st>>>(d, c, g, w, q, a);
   }
   k_adj_nodal<<<blocks_for(n0, kTPBN), kTPBN, 0, st>>>(d, c, g, w, q, a);
   const long long ei = d.ni + 2 * kG, ej = d.nj + 2 * kG;

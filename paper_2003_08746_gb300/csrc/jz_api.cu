@@ -372,7 +372,7 @@ int stats_sample(jz_solver* s) {
 
 // ---- discrete adjoint: forward stages from an explicit Q^n --------------------------
 // A pair-form solver advances the states in pair arithmetic (its reverse sweep also regenerates
-// the intermediates the FP64 transposed kernels read with the pair nodal and viscous passes).
+// the intermediates the transposed kernels read with the pair nodal and viscous passes).
 int fwd_stage(jz_solver* s, const jz::State& in, const jz::State& qn, const jz::State& out, int l) {
   const jz::Dims& d = s->grid->d;
   const jz::GridDev& g = s->grid->g;
@@ -1012,7 +1012,8 @@ int jz_adjoint_step(jz_solver* s, const double* forcing_amps, int nsteps, int ck
           JZ_RUN(JZ_PROF_NODAL, jz::nodal64(d, s->c, g, s->w, *st[l], s->st));
           JZ_RUN(JZ_PROF_VISCOUS, jz::viscous64(d, s->c, g, s->w, *st[l], s->st));
         }
-        JZ_RUN(JZ_PROF_ADJOINT, jz::adj_stage(d, s->c, g, s->w, *st[l], a, s->pair, s->st));
+        JZ_RUN(JZ_PROF_ADJOINT, jz::adj_stage(d, s->c, g, s->w, *st[l], a, s->pair ? &s->mdf : nullptr,
+                                              s->pair ? &s->qdf : nullptr, s->st));
       }
       JZ_RUN(JZ_PROF_ADJOINT, jz::adj_add_qn(d, a, s->st));
     }
