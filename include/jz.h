@@ -65,9 +65,9 @@ extern "C" {
                                  and state, 152; no stored face fluxes, -120).
                                  jz_adjoint_step on such a solver advances
                                  the states, regenerates the intermediates and
-                                 runs the transposed viscous pass in pair
-                                 arithmetic, the other transposed passes in
-                                 FP64.                                        */
+                                 runs the transposed passes in pair arithmetic
+                                 (adjoint arrays, gathers and the boundary-
+                                 condition adjoints in FP64).                 */
 
 #define JZ_N_MODES 8          /* azimuthal forcing modes m = 0..7            */
 #define JZ_N_FREQ  4          /* forcing frequencies (Strouhal numbers)      */

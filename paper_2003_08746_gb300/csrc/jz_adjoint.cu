@@ -13,32 +13,12 @@
 // first argument on ties, |x| and sqrt(x) at 0 have derivative 0, cbrt'(0)
 // is 0, and the supersonic/subsonic and inflow/outflow switches take the
 // branch the forward pass took.
-#include "jz_df.cuh"
-#include "jz_internal.cuh"
+#include "jz_adjgather.cuh"
 
 namespace jz {
 namespace {
 
 constexpr int kTPB = 256;
-
-__device__ __forceinline__ bool in_box(const Dims& d, int i, int j, int k) {
-  return i >= -kG && i <= d.ni + 1 && j >= -kG && j <= d.nj + 1 && k >= -kG && k <= d.nk + 1;
-}
-
-// value of a padded field at (i, j, k) + offset along dir, 0 outside the padded box
-__device__ __forceinline__ double nb(const Dims& d, const double* f, int i, int j, int k, int dir, int off) {
-  int ii = i, jj = j, kk = k;
-  if (dir == 0) ii += off; else if (dir == 1) jj += off; else kk += off;
-  return in_box(d, ii, jj, kk) ? f[pidx(d, ii, jj, kk)] : 0.0;
-}
-
-// A forward intermediate (u, v, w, T, p, mu, the sensors, Lambda) at padded index p: FP64, or the
-// double-float pair the pair-form passes store in the same array, read back as hi + lo.
-template <bool PAIR>
-__device__ __forceinline__ double wv(const double* f, long long p) {
-  if (PAIR) return df_to_f64(df_load(reinterpret_cast<const float2*>(f), p));
-  return f[p];
-}
 
 __device__ __forceinline__ double sgn(double x) { return x > 0.0 ? 1.0 : (x < 0.0 ? -1.0 : 0.0); }
 
@@ -83,8 +63,7 @@ __global__ void k_adj_update(Dims d, GridDev g, Adj64 a, double adt) {
   }
 }
 
-// ---- dissipation faces -------------------------------------------------------------
-template <bool PAIR>
+// ---- dissipation faces (FP64 solvers; pair solvers: jz_adjointdf.cu) ----------------
 __global__ void k_adj_faces(Dims d, Consts c, Work64 w, State q, Adj64 a) {
   Box b{-1, -1, -1, d.ni + 1, d.nj + 1, d.nk + 1};
   int i, j, k;
@@ -93,12 +72,12 @@ __global__ void k_adj_faces(Dims d, Consts c, Work64 w, State q, Adj64 a) {
   const long long s[3] = {1, d.sj, d.sk};
   for (int dir = 0; dir < 3; ++dir) {
     const long long sd = s[dir];
-    const double nu0 = wv<PAIR>(w.nu[dir], p), nu1 = wv<PAIR>(w.nu[dir], p + sd);
+    const double nu0 = w.nu[dir][p], nu1 = w.nu[dir][p + sd];
     const bool first = nu0 >= nu1;
     const double eps2 = c.kappa2 * (first ? nu0 : nu1);
     const double k4 = c.kappa4 - eps2;
     const double eps4 = k4 > 0.0 ? k4 : 0.0;
-    const double Lf = 0.5 * (wv<PAIR>(w.Lam[dir], p) + wv<PAIR>(w.Lam[dir], p + sd));
+    const double Lf = 0.5 * (w.Lam[dir][p] + w.Lam[dir][p + sd]);
     double lf = 0.0, e2b = 0.0, e4b = 0.0;
     for (int m = 0; m < 5; ++m) {
       const double* Q = q.q[m];
@@ -122,7 +101,7 @@ __global__ void k_adj_faces(Dims d, Consts c, Work64 w, State q, Adj64 a) {
   }
 }
 
-// ---- viscous pass and pressure sensor (FP64 solvers; pair solvers: k_adj_visc_df) ----
+// ---- viscous pass and pressure sensor (FP64 solvers; pair solvers: jz_adjointdf.cu) --
 __global__ void k_adj_visc(Dims d, Consts c, GridDev g, Work64 w, State q, Adj64 a) {
   Box b{-1, -1, -1, d.ni + 2, d.nj + 2, d.nk + 2};
   int i, j, k;
@@ -219,7 +198,7 @@ __global__ void k_adj_visc(Dims d, Consts c, GridDev g, Work64 w, State q, Adj64
   }
 }
 
-// ---- nodal pass: gathers, then the reverse of primitives/fluxes/spectral radii --------
+// ---- nodal pass: gathers, then the reverse of primitives/fluxes/spectral radii (FP64) --
 // 128-thread blocks, three per SM: the pass needs ~170 registers, and three small blocks
 // keep more warps resident than one 256-thread block (4% faster gradient).
 constexpr int kTPBN = 128;
@@ -228,43 +207,14 @@ __global__ void __launch_bounds__(kTPBN, 3) k_adj_nodal(Dims d, Consts c, GridDe
   int i, j, k;
   if (!box_coord(b, blockIdx.x * (long long)blockDim.x + threadIdx.x, i, j, k)) return;
   const long long p = pidx(d, i, j, k);
-  // gathers
-  double fb[4];
-  for (int n = 0; n < 4; ++n) {
-    double v = n < 3 ? nb(d, a.ubd[n], i, j, k, 0, 0) : 0.0;
-    for (int dir = 0; dir < 3; ++dir)
-      v += 0.5 * (nb(d, a.G[n][dir], i, j, k, dir, -1) - nb(d, a.G[n][dir], i, j, k, dir, 1));
-    fb[n] = v;
-  }
-  double pb = 0.0;
-  for (int dir = 0; dir < 3; ++dir)
-    pb += nb(d, a.c0[dir], i, j, k, 0, 0) + nb(d, a.cpm[dir], i, j, k, dir, -1) + nb(d, a.cpm[dir], i, j, k, dir, 1);
-  double Eb[3][5], Lamb[3];
-  for (int dir = 0; dir < 3; ++dir) {
-    for (int m = 0; m < 5; ++m)
-      Eb[dir][m] = 0.5 * (nb(d, a.acc[m], i, j, k, dir, -1) - nb(d, a.acc[m], i, j, k, dir, 1));
-    Lamb[dir] = nb(d, a.lfh[dir], i, j, k, 0, 0) + nb(d, a.lfh[dir], i, j, k, dir, -1);
-  }
-  // dissipation: node n receives, from faces n-2 .. n+1 (f = face n + o), the adjoints of the
-  // differences it enters: d3(f-2) + d1(f-1) - 3 d3(f-1) - d1(f) + 3 d3(f) - d3(f+1), with
-  // d1(f) = Db(f) ca2(f), d3(f) = -Db(f) ca4(f), Db(f) = acc(f+1) - acc(f) (zero beyond the box)
-  double qb[5] = {0, 0, 0, 0, 0};
-  for (int dir = 0; dir < 3; ++dir) {
-    double c2[4], c4[4];           // faces n-2, n-1, n, n+1
-    for (int o = 0; o < 4; ++o) {
-      c2[o] = nb(d, a.ca2[dir], i, j, k, dir, o - 2);
-      c4[o] = nb(d, a.ca4[dir], i, j, k, dir, o - 2);
-    }
-    for (int m = 0; m < 5; ++m) {
-      const double am2 = nb(d, a.acc[m], i, j, k, dir, -2), am1 = nb(d, a.acc[m], i, j, k, dir, -1),
-                   a0 = nb(d, a.acc[m], i, j, k, 0, 0), ap1 = nb(d, a.acc[m], i, j, k, dir, 1),
-                   ap2 = nb(d, a.acc[m], i, j, k, dir, 2);
-      const double D0 = am1 - am2, D1 = a0 - am1, D2 = ap1 - a0, D3 = ap2 - ap1;
-      qb[m] += -D0 * c4[0] + D1 * c2[1] + 3.0 * (D1 * c4[1]) - D2 * c2[2] - 3.0 * (D2 * c4[2]) + D3 * c4[3];
-    }
-  }
-  qb[0] += nb(d, a.rhob, i, j, k, 0, 0);
-  double mub = nb(d, a.mub, i, j, k, 0, 0);
+  NodalGathers G;
+  nodal_gathers(d, a, i, j, k, G);
+  double* fb = G.fb;
+  double pb = G.pb;
+  double (*Eb)[5] = G.Eb;
+  double* Lamb = G.Lamb;
+  double* qb = G.qb;
+  const double mub = G.mub;
   // forward nodal quantities
   double Q[5];
   load5(q, p, Q);
@@ -651,14 +601,15 @@ cudaError_t adj_stage(const Dims& d, const Consts& c, const GridDev& g, const Wo
   const long long n1 = (long long)(d.ni + 2) * (d.nj + 2) * (d.nk + 2);
   const long long nf = (long long)(d.ni + 1) * (d.nj + 1) * (d.nk + 1);
   if (pair) {
-    k_adj_faces<true><<<blocks_for(nf, kTPB), kTPB, 0, st>>>(d, c, w, q, a);
-    const cudaError_t e = adj_visc_df(d, c, *mdf, w, *qdf, a, st);
+    cudaError_t e = adj_faces_df(d, c, w, *qdf, a, st);
+    if (e == cudaSuccess) e = adj_visc_df(d, c, *mdf, w, *qdf, a, st);
+    if (e == cudaSuccess) e = adj_nodal_df(d, c, *mdf, *qdf, a, st);
     if (e != cudaSuccess) return e;
   } else {
-    k_adj_faces<false><<<blocks_for(nf, kTPB), kTPB, 0, st>>>(d, c, w, q, a);
+    k_adj_faces<<<blocks_for(nf, kTPB), kTPB, 0, st>>>(d, c, w, q, a);
     k_adj_visc<<<blocks_for(n1, kTPB), kTPB, 0, st>>>(d, c, g, w, q, a);
+    k_adj_nodal<<<blocks_for(n0, kTPBN), kTPBN, 0, st>>>(d, c, g, w, q, a);
   }
-  k_adj_nodal<<<blocks_for(n0, kTPBN), kTPBN, 0, st>>>(d, c, g, w, q, a);
   const long long ei = d.ni + 2 * kG, ej = d.nj + 2 * kG;
   const long long ng = 4 * ei * ej + 4 * ei * d.nk + 4LL * d.nj * d.nk;
   k_adj_ghost<<<blocks_for(ng, kTPB), kTPB, 0, st>>>(d, a);

@@ -1,0 +1,301 @@
+// Transposed passes of the discrete adjoint for a pair-form solver (see jz_adjoint.cu for the
+// FP64 form and the structure of the reverse sweep): the face, viscous-and-sensor and nodal
+// passes in double-float arithmetic on the pair intermediates that the pair nodal and viscous
+// passes regenerated (u, v, w, T, p, mu, the sensors, Lambda, the pair copies of Q and of the
+// metrics).  The adjoint arrays stay FP64; the gathers sum them in FP64, and values cross
+// between the two representations by df_of and df_to_f64.
+#include "jz_adjgather.cuh"
+#include "jz_dfconsts.cuh"
+
+namespace jz {
+namespace {
+
+// Transposed dissipation faces of the discrete adjoint (jz_adjoint.cu, k_adj_faces) for a
+// pair-form solver, in double-float arithmetic on the pair copies of Q, the sensors and Lambda;
+// the differences of the FP64 adjoint array acc are formed in FP64 and converted, the outputs
+// converted back.  Faces n + 1/2, n in [-1, n_dir - 1].
+__global__ void k_adj_faces_df(Dims d, ConstsDF c, Work64 w, QDF qdf, Adj64 a) {
+  Box b{-1, -1, -1, d.ni + 1, d.nj + 1, d.nk + 1};
+  int i, j, k;
+  if (!box_coord(b, blockIdx.x * (long long)blockDim.x + threadIdx.x, i, j, k)) return;
+  const long long p = pidx(d, i, j, k);
+  const long long s[3] = {1, d.sj, d.sk};
+  for (int dir = 0; dir < 3; ++dir) {
+    const long long sd = s[dir];
+    const dfl nu0 = ld(w.nu[dir], p), nu1 = ld(w.nu[dir], p + sd);
+    const bool first = df_ge(nu0, nu1);
+    const dfl eps2 = df_mul(c.kappa2, first ? nu0 : nu1);
+    const dfl k4 = df_sub(c.kappa4, eps2);
+    const bool pos4 = df_gt0(k4);
+    const dfl eps4 = pos4 ? k4 : df_from(0.f);
+    const dfl Lf = df_scale(df_add(ld(w.Lam[dir], p), ld(w.Lam[dir], p + sd)), 0.5f);
+    dfl lf = df_from(0.f), e2b = df_from(0.f), e4b = df_from(0.f);
+    for (int m = 0; m < 5; ++m) {
+      const double* Q = qdf.q[m];
+      const dfl q0 = ld(Q, p), q1 = ld(Q, p + sd), q2 = ld(Q, p + 2 * sd), qm = ld(Q, p - sd);
+      const dfl d1 = df_sub(q1, q0);
+      const dfl d3 = df_sub(df_add(df_sub(q2, df_mul_f(q1, 3.f)), df_mul_f(q0, 3.f)), qm);
+      const dfl Db = df_of(a.acc[m][p + sd] - a.acc[m][p]);
+      lf = df_fma(Db, df_sub(df_mul(eps2, d1), df_mul(eps4, d3)), lf);
+      const dfl DL = df_mul(Db, Lf);
+      e2b = df_fma(DL, d1, e2b);
+      e4b = df_sub(e4b, df_mul(DL, d3));
+    }
+    a.ca2[dir][p] = df_to_f64(df_mul(Lf, eps2));
+    a.ca4[dir][p] = df_to_f64(df_mul(Lf, eps4));
+    if (pos4) e2b = df_sub(e2b, e4b);
+    const double nub = df_to_f64(df_mul(c.kappa2, e2b));
+    a.nb0[dir][p] = first ? nub : 0.0;
+    a.nb1[dir][p] = first ? 0.0 : nub;
+    a.lfh[dir][p] = df_to_f64(df_scale(lf, 0.5f));
+  }
+}
+
+// Transposed viscous pass and pressure sensor of the discrete adjoint (jz_adjoint.cu, k_adj_visc)
+// for a pair-form solver: the same reverse sweep through gradients, strain rate, eddy viscosity,
+// stresses, heat flux and sensors, in double-float arithmetic on the pair intermediates the pair
+// passes regenerated (u, v, w, T, p, mu, the pair copies of Q and of the metrics).  The adjoint
+// arrays stay FP64: the incoming differences are formed in FP64 and converted, the outputs
+// converted back.  Nodes within one layer of the real region.
+__global__ void k_adj_visc_df(Dims d, ConstsDF c, DFMetrics M, Work64 w, QDF qdf, Adj64 a) {
+  Box b{-1, -1, -1, d.ni + 2, d.nj + 2, d.nk + 2};
+  int i, j, k;
+  if (!box_coord(b, blockIdx.x * (long long)blockDim.x + threadIdx.x, i, j, k)) return;
+  const long long p = pidx(d, i, j, k);
+  const long long s[3] = {1, d.sj, d.sk};
+  // adjoint of H^dir (components 1..4 carry the viscous flux)
+  dfl Hb[3][4];
+  for (int dir = 0; dir < 3; ++dir)
+    for (int m = 0; m < 4; ++m) Hb[dir][m] = df_of(0.5 * (a.acc[m + 1][p - s[dir]] - a.acc[m + 1][p + s[dir]]));
+  // forward viscous quantities
+  const double* f[4] = {w.u, w.v, w.w, w.T};
+  dfl S[3][3];
+  for (int dir = 0; dir < 3; ++dir)
+    for (int cc = 0; cc < 3; ++cc) S[dir][cc] = df_load(M.S[3 * dir + cc], p);
+  const dfl iV = df_load(M.invV, p);
+  dfl L[4][3];
+  for (int n = 0; n < 4; ++n) {
+    dfl dd[3];
+    for (int dir = 0; dir < 3; ++dir) dd[dir] = df_scale(df_sub(ld(f[n], p + s[dir]), ld(f[n], p - s[dir])), 0.5f);
+    for (int jj = 0; jj < 3; ++jj)
+      L[n][jj] = df_mul(iV, df_fma(S[2][jj], dd[2], df_fma(S[1][jj], dd[1], df_mul(S[0][jj], dd[0]))));
+  }
+  dfl Sij[3][3];
+  for (int x = 0; x < 3; ++x)
+    for (int y = 0; y < 3; ++y) Sij[x][y] = df_scale(df_add(L[x][y], L[y][x]), 0.5f);
+  const dfl div = df_add(df_add(Sij[0][0], Sij[1][1]), Sij[2][2]);
+  dfl SS = df_from(0.f);
+  for (int x = 0; x < 3; ++x)
+    for (int y = 0; y < 3; ++y) SS = df_fma(Sij[x][y], Sij[x][y], SS);
+  const dfl Smod = df_sqrt(df_scale(SS, 2.f));
+  const dfl mu = ld(w.mu, p);
+  const dfl csd = df_mul(c.C_s, df_load(M.Delta, p));
+  const dfl cs2 = df_mul(csd, csd);
+  const dfl rho = ld(qdf.q[0], p);
+  const dfl mu_sgs = df_mul(df_mul(rho, cs2), Smod);
+  const dfl mu_eff = df_add(mu, mu_sgs);
+  const dfl k_eff = df_add(df_mul(mu, c.k_lam), df_mul(mu_sgs, c.k_sgs));
+  const dfl d3 = df_mul(div, c.third);
+  const dfl m2 = df_scale(mu_eff, 2.f);
+  dfl dev[3][3];                                       // S_ij - delta_ij div/3
+  for (int x = 0; x < 3; ++x)
+    for (int y = 0; y < 3; ++y) dev[x][y] = x == y ? df_sub(Sij[x][y], d3) : Sij[x][y];
+  const dfl vel[3] = {ld(w.u, p), ld(w.v, p), ld(w.w, p)};
+  // reverse: F^dir_m = S^dir_j F_j,m ; H = E - F
+  dfl taub[3][3], ubd[3], keb = df_from(0.f), L3b[3];
+  for (int x = 0; x < 3; ++x) {
+    ubd[x] = df_from(0.f);
+    L3b[x] = df_from(0.f);
+    for (int y = 0; y < 3; ++y) taub[x][y] = df_from(0.f);
+  }
+  for (int jj = 0; jj < 3; ++jj) {
+    dfl Fb[4];
+    for (int m = 0; m < 4; ++m)
+      Fb[m] = df_neg(df_fma(S[2][jj], Hb[2][m], df_fma(S[1][jj], Hb[1][m], df_mul(S[0][jj], Hb[0][m]))));
+    for (int x = 0; x < 3; ++x) taub[x][jj] = df_add(taub[x][jj], Fb[x]);
+    const dfl e = Fb[3];
+    for (int x = 0; x < 3; ++x) {
+      ubd[x] = df_fma(e, df_mul(m2, dev[x][jj]), ubd[x]);         // e tau_x,jj
+      taub[x][jj] = df_fma(e, vel[x], taub[x][jj]);
+    }
+    keb = df_fma(e, L[3][jj], keb);
+    L3b[jj] = df_fma(e, k_eff, L3b[jj]);
+  }
+  dfl mueb = df_from(0.f), Sijb[3][3], tr = df_from(0.f);
+  for (int x = 0; x < 3; ++x)
+    for (int y = 0; y < 3; ++y) {
+      mueb = df_fma(taub[x][y], df_scale(dev[x][y], 2.f), mueb);
+      Sijb[x][y] = df_mul(m2, taub[x][y]);
+    }
+  for (int x = 0; x < 3; ++x) tr = df_add(tr, taub[x][x]);
+  const dfl divb = df_neg(df_mul(df_mul(mu_eff, df_scale(c.third, 2.f)), tr));
+  for (int x = 0; x < 3; ++x) Sijb[x][x] = df_add(Sijb[x][x], divb);
+  const dfl mub = df_add(df_mul(keb, c.k_lam), mueb);
+  const dfl musb = df_add(df_mul(keb, c.k_sgs), mueb);
+  const dfl rhob = df_mul(df_mul(musb, cs2), Smod);
+  const dfl Smodb = df_mul(df_mul(musb, rho), cs2);
+  const dfl SSb = df_gt0(Smod) ? df_mul(Smodb, df_rcp(Smod)) : df_from(0.f);
+  for (int x = 0; x < 3; ++x)
+    for (int y = 0; y < 3; ++y) Sijb[x][y] = df_fma(df_scale(Sij[x][y], 2.f), SSb, Sijb[x][y]);
+  dfl Lb[4][3];
+  for (int x = 0; x < 3; ++x)
+    for (int y = 0; y < 3; ++y) Lb[x][y] = df_scale(df_add(Sijb[x][y], Sijb[y][x]), 0.5f);
+  for (int y = 0; y < 3; ++y) Lb[3][y] = L3b[y];
+  for (int n = 0; n < 4; ++n)
+    for (int dir = 0; dir < 3; ++dir)
+      a.G[n][dir][p] =
+          df_to_f64(df_mul(iV, df_fma(S[dir][2], Lb[n][2], df_fma(S[dir][1], Lb[n][1], df_mul(S[dir][0], Lb[n][0])))));
+  for (int x = 0; x < 3; ++x) a.ubd[x][p] = df_to_f64(ubd[x]);
+  a.mub[p] = df_to_f64(mub);
+  a.rhob[p] = df_to_f64(rhob);
+  // pressure sensor nu = |N| / Dn
+  const dfl pc2 = df_scale(ld(w.p, p), 2.f);
+  for (int dir = 0; dir < 3; ++dir) {
+    const double nub = a.nb0[dir][p] + a.nb1[dir][p - s[dir]];
+    const dfl sum = df_add(ld(w.p, p + s[dir]), ld(w.p, p - s[dir]));
+    const dfl N = df_sub(sum, pc2), Dn = df_add(sum, pc2);
+    const dfl iD = df_rcp(Dn);
+    const dfl nu = df_mul(df_abs(N), iD);
+    const float sg = N.hi > 0.f ? 1.f : (N.hi < 0.f ? -1.f : 0.f);
+    const dfl nbD = df_mul(df_of(nub), iD);
+    a.cpm[dir][p] = df_to_f64(df_mul(nbD, df_sub(df_from(sg), nu)));
+    a.c0[dir][p] = df_to_f64(df_mul(nbD, df_scale(df_add(df_from(sg), nu), -2.f)));
+  }
+}
+
+
+// Transposed nodal pass (jz_adjoint.cu, k_adj_nodal) for a pair-form solver: the gathers in
+// FP64, then the reverse of the anisotropic spectral radii, the inviscid fluxes, Sutherland's
+// law and the primitives in double-float arithmetic on the pair copies of Q and the metrics.
+// Every padded node.  Four 128-thread blocks per SM (128 registers, some spilled): 1.79 s per
+// 200-step gradient on 128 x 96 x 64, against 1.83 at three (168) and 1.91 at two (254).
+constexpr int kTPBN = 128;
+__global__ void __launch_bounds__(kTPBN, 4) k_adj_nodal_df(Dims d, ConstsDF c, DFMetrics M, QDF qdf, Adj64 a) {
+  Box b{-kG, -kG, -kG, d.ni + 2 * kG, d.nj + 2 * kG, d.nk + 2 * kG};
+  int i, j, k;
+  if (!box_coord(b, blockIdx.x * (long long)blockDim.x + threadIdx.x, i, j, k)) return;
+  const long long p = pidx(d, i, j, k);
+  NodalGathers G;
+  nodal_gathers(d, a, i, j, k, G);
+  dfl ub[3] = {df_of(G.fb[0]), df_of(G.fb[1]), df_of(G.fb[2])};
+  dfl Tb = df_of(G.fb[3]);
+  dfl pb = df_of(G.pb);
+  dfl qb[5];
+  for (int m = 0; m < 5; ++m) qb[m] = df_of(G.qb[m]);
+  const dfl mub = df_of(G.mub);
+  // forward nodal quantities
+  dfl Q[5];
+  for (int m = 0; m < 5; ++m) Q[m] = ld(qdf.q[m], p);
+  const dfl rho = Q[0];
+  const dfl ir = df_rcp(rho);
+  const dfl u[3] = {df_mul(Q[1], ir), df_mul(Q[2], ir), df_mul(Q[3], ir)};
+  const dfl pr = df_mul(c.gm1, df_sub(Q[4], df_scale(df_fma(Q[3], u[2], df_fma(Q[2], u[1], df_mul(Q[1], u[0]))), 0.5f)));
+  const dfl T = df_mul(df_mul(c.gamma, pr), ir);
+  const dfl aa = df_sqrt(T);
+  const dfl iTS = df_rcp(df_add(T, c.S_hat));
+  const dfl mu = df_mul(df_mul(c.mu_sut, df_mul(T, aa)), iTS);
+  dfl Sv[3][3], Smag[3], U[3], lam[3];
+  for (int dir = 0; dir < 3; ++dir) {
+    for (int cc = 0; cc < 3; ++cc) Sv[dir][cc] = df_load(M.S[3 * dir + cc], p);
+    Smag[dir] = df_load(M.Smag[dir], p);
+    U[dir] = df_fma(Sv[dir][2], u[2], df_fma(Sv[dir][1], u[1], df_mul(Sv[dir][0], u[0])));
+    lam[dir] = df_fma(aa, Smag[dir], df_abs(U[dir]));
+  }
+  // anisotropic scaling Lambda_d = lam_d + lo_d (hi_e + hi_f)
+  const dfl Lamb[3] = {df_of(G.Lamb[0]), df_of(G.Lamb[1]), df_of(G.Lamb[2])};
+  dfl lamb[3] = {Lamb[0], Lamb[1], Lamb[2]};
+  {
+    dfl lo[3], hi[3], dlo[3], dhi[3];
+    for (int dd = 0; dd < 3; ++dd) {
+      if (c.sigma_is_two_thirds) {
+        df_cbrt_pair(lam[dd], lo[dd], hi[dd]);                       // lam^(1/3), lam^(2/3)
+        dlo[dd] = df_gt0(lo[dd]) ? df_rcp(df_mul_f(hi[dd], 3.f)) : df_from(0.f);   // d lo / d lam
+        dhi[dd] = df_mul(df_scale(lo[dd], 2.f), dlo[dd]);          // d hi / d lam
+      } else {
+        // a general exponent through FP64 pow (not on the benchmark path)
+        const double l = df_to_f64(lam[dd]);
+        const bool pos = l > 0.0;
+        const double lo64 = pos ? pow(l, 1.0 - c.sigma) : 0.0, hi64 = pos ? pow(l, c.sigma) : 0.0;
+        lo[dd] = df_of(lo64);
+        hi[dd] = df_of(hi64);
+        dlo[dd] = df_of(pos ? (1.0 - c.sigma) * lo64 / l : 0.0);
+        dhi[dd] = df_of(pos ? c.sigma * hi64 / l : 0.0);
+      }
+    }
+    dfl lob[3], hib[3];
+    for (int dd = 0; dd < 3; ++dd) lob[dd] = hib[dd] = df_from(0.f);
+    const int e1[3] = {1, 0, 0}, e2[3] = {2, 2, 1};
+    for (int dd = 0; dd < 3; ++dd) {
+      lob[dd] = df_fma(Lamb[dd], df_add(hi[e1[dd]], hi[e2[dd]]), lob[dd]);
+      const dfl Ll = df_mul(Lamb[dd], lo[dd]);
+      hib[e1[dd]] = df_add(hib[e1[dd]], Ll);
+      hib[e2[dd]] = df_add(hib[e2[dd]], Ll);
+    }
+    for (int dd = 0; dd < 3; ++dd) lamb[dd] = df_fma(hib[dd], dhi[dd], df_fma(lob[dd], dlo[dd], lamb[dd]));
+  }
+  dfl ab = df_from(0.f);
+  const dfl h0 = df_add(Q[4], pr);
+  for (int dir = 0; dir < 3; ++dir) {
+    const dfl E[5] = {df_of(G.Eb[dir][0]), df_of(G.Eb[dir][1]), df_of(G.Eb[dir][2]), df_of(G.Eb[dir][3]),
+                      df_of(G.Eb[dir][4])};
+    const float sg = U[dir].hi > 0.f ? 1.f : (U[dir].hi < 0.f ? -1.f : 0.f);
+    dfl Ub = df_mul_f(lamb[dir], sg);
+    ab = df_fma(lamb[dir], Smag[dir], ab);
+    // E = [rho U, m_i U + p S_i, (e + p) U]
+    qb[0] = df_fma(E[0], U[dir], qb[0]);
+    Ub = df_fma(E[0], rho, Ub);
+    for (int x = 0; x < 3; ++x) {
+      qb[1 + x] = df_fma(E[1 + x], U[dir], qb[1 + x]);
+      Ub = df_fma(E[1 + x], Q[1 + x], Ub);
+      pb = df_fma(E[1 + x], Sv[dir][x], pb);
+    }
+    qb[4] = df_fma(E[4], U[dir], qb[4]);
+    pb = df_fma(E[4], U[dir], pb);
+    Ub = df_fma(E[4], h0, Ub);
+    for (int x = 0; x < 3; ++x) ub[x] = df_fma(Ub, Sv[dir][x], ub[x]);
+  }
+  // Sutherland mu(T): d mu / dT = mu (1.5/T - 1/(T + S))
+  Tb = df_fma(mub, df_mul(mu, df_sub(df_mul_f(df_rcp(T), 1.5f), iTS)), Tb);
+  Tb = df_fma(ab, df_scale(df_rcp(aa), 0.5f), Tb);
+  pb = df_fma(Tb, df_mul(c.gamma, ir), pb);
+  qb[0] = df_sub(qb[0], df_mul(df_mul(Tb, T), ir));
+  // reverse of u_i = m_i / rho, p = (gamma-1)(e - m.u/2)
+  qb[4] = df_fma(c.gm1, pb, qb[4]);
+  const dfl keb = df_scale(df_neg(df_mul(c.gm1, pb)), 0.5f);      // half the adjoint of m.u
+  for (int x = 0; x < 3; ++x) {
+    qb[1 + x] = df_fma(keb, u[x], qb[1 + x]);
+    ub[x] = df_fma(keb, Q[1 + x], ub[x]);
+  }
+  dfl sum = df_from(0.f);
+  for (int x = 0; x < 3; ++x) {
+    qb[1 + x] = df_fma(ub[x], ir, qb[1 + x]);
+    sum = df_fma(ub[x], u[x], sum);
+  }
+  qb[0] = df_sub(qb[0], df_mul(sum, ir));
+  for (int m = 0; m < 5; ++m) a.lam[m][p] = df_to_f64(qb[m]);
+}
+
+}  // namespace
+
+cudaError_t adj_nodal_df(const Dims& d, const Consts& c, const DFMetrics& M, const QDF& qdf, const Adj64& a,
+                         cudaStream_t st) {
+  const long long n0 = (long long)(d.ni + 2 * kG) * (d.nj + 2 * kG) * (d.nk + 2 * kG);
+  k_adj_nodal_df<<<blocks_for(n0, kTPBN), kTPBN, 0, st>>>(d, make_cdf(c), M, qdf, a);
+  return cudaGetLastError();
+}
+
+cudaError_t adj_faces_df(const Dims& d, const Consts& c, const Work64& w, const QDF& qdf, const Adj64& a,
+                         cudaStream_t st) {
+  const long long nf = (long long)(d.ni + 1) * (d.nj + 1) * (d.nk + 1);
+  k_adj_faces_df<<<blocks_for(nf, 256), 256, 0, st>>>(d, make_cdf(c), w, qdf, a);
+  return cudaGetLastError();
+}
+
+cudaError_t adj_visc_df(const Dims& d, const Consts& c, const DFMetrics& M, const Work64& w, const QDF& qdf,
+                        const Adj64& a, cudaStream_t st) {
+  const long long n1 = (long long)(d.ni + 2) * (d.nj + 2) * (d.nk + 2);
+  k_adj_visc_df<<<blocks_for(n1, 256), 256, 0, st>>>(d, make_cdf(c), M, w, qdf, a);
+  return cudaGetLastError();
+}
+
+}  // namespace jz

@@ -366,11 +366,16 @@ cudaError_t flow_final(const Dims& d, const double* mean, const double* m2, long
 // adjoint (jz_adjoint.cu)
 cudaError_t adj_update(const Dims& d, const GridDev& g, const Adj64& a, double adt, cudaStream_t st);
 // mdf, qdf non-null: a pair-form solver, whose forward intermediates in w are double-float pairs;
-// its transposed viscous pass runs in pair arithmetic (adj_visc_df, jz_stagedf.cu)
+// its transposed face, viscous and nodal passes run in pair arithmetic (adj_faces_df,
+// adj_visc_df, adj_nodal_df, jz_adjointdf.cu)
 cudaError_t adj_stage(const Dims& d, const Consts& c, const GridDev& g, const Work64& w, const State& q,
                       const Adj64& a, const DFMetrics* mdf, const QDF* qdf, cudaStream_t st);
 cudaError_t adj_visc_df(const Dims& d, const Consts& c, const DFMetrics& M, const Work64& w, const QDF& qdf,
                         const Adj64& a, cudaStream_t st);
+cudaError_t adj_faces_df(const Dims& d, const Consts& c, const Work64& w, const QDF& qdf, const Adj64& a,
+                         cudaStream_t st);
+cudaError_t adj_nodal_df(const Dims& d, const Consts& c, const DFMetrics& M, const QDF& qdf, const Adj64& a,
+                         cudaStream_t st);
 cudaError_t adj_add_qn(const Dims& d, const Adj64& a, cudaStream_t st);
 cudaError_t adj_bcs(const Dims& d, const Consts& c, const GridDev& g, const Inflow& in, const State& q,
                     const Adj64& a, double ts, cudaStream_t st);

@@ -11,8 +11,7 @@
 //
 // The nodal and viscous passes are launched on 3-D grids (64 x 4 threads per block along i and j,
 // one block row per k), so no pass divides a flat index.
-#include "jz_df.cuh"
-#include "jz_internal.cuh"
+#include "jz_dfconsts.cuh"
 
 namespace jz {
 namespace {
@@ -33,36 +32,6 @@ __device__ __forceinline__ bool advanced(const Dims& d, int i, int j) {
   return d.topo != JZ_TOPO_JET || (i >= 1 && i <= d.ni - 2 && j >= 1 && j <= d.nj - 2);
 }
 
-// Constants as pairs (hi, lo) of their FP64 values: an FP32 constant such as 0.4 would put an
-// error of ~1e-8 into every product.
-struct ConstsDF {
-  dfl gamma, gm1, gm1_half, S_hat, kappa2, kappa4, C_s, k_lam, k_sgs;
-  dfl mu_sut;        // mu_ref (1 + S_hat)
-  dfl third;         // 1/3
-  int sigma_is_two_thirds;
-  double sigma;
-};
-
-__device__ __forceinline__ dfl ld(const double* a, long long p) { return df_load(reinterpret_cast<const float2*>(a), p); }
-__device__ __forceinline__ void st(double* a, long long p, dfl v) { df_store(reinterpret_cast<float2*>(a), p, v); }
-
-// Anisotropic spectral radius lambda_d + lambda_d^(1-sigma) (lambda_e^sigma + lambda_f^sigma).
-__device__ __forceinline__ void aniso_df(const ConstsDF& c, const dfl lam[3], dfl Lam[3]) {
-  dfl lo[3], hi[3];
-  if (c.sigma_is_two_thirds) {
-    for (int d = 0; d < 3; ++d) df_cbrt_pair(lam[d], lo[d], hi[d]);
-  } else {
-    // a general exponent through FP64 pow (not on the benchmark path)
-    for (int d = 0; d < 3; ++d) {
-      const double l = df_to_f64(lam[d]);
-      lo[d] = df_of(l > 0.0 ? pow(l, 1.0 - c.sigma) : 0.0);
-      hi[d] = df_of(l > 0.0 ? pow(l, c.sigma) : 0.0);
-    }
-  }
-  Lam[0] = df_fma(lo[0], df_add(hi[1], hi[2]), lam[0]);
-  Lam[1] = df_fma(lo[1], df_add(hi[0], hi[2]), lam[1]);
-  Lam[2] = df_fma(lo[2], df_add(hi[0], hi[1]), lam[2]);
-}
 
 // A: every padded node.  Primitives, Sutherland mu, spectral radii and their anisotropic
 // scaling; the double-float copy of Q for the viscous and faces passes; at stage 1 also the CFL
@@ -315,118 +284,6 @@ __global__ void __launch_bounds__(FX* FY, 2) k_faces_update_df(Dims d, ConstsDF 
   }
 }
 
-// Transposed viscous pass and pressure sensor of the discrete adjoint (jz_adjoint.cu, k_adj_visc)
-// for a pair-form solver: the same reverse sweep through gradients, strain rate, eddy viscosity,
-// stresses, heat flux and sensors, in double-float arithmetic on the pair intermediates the pair
-// passes regenerated (u, v, w, T, p, mu, the pair copies of Q and of the metrics).  The adjoint
-// arrays stay FP64: the incoming differences are formed in FP64 and converted, the outputs
-// converted back.  Nodes within one layer of the real region.
-__global__ void k_adj_visc_df(Dims d, ConstsDF c, DFMetrics M, Work64 w, QDF qdf, Adj64 a) {
-  Box b{-1, -1, -1, d.ni + 2, d.nj + 2, d.nk + 2};
-  int i, j, k;
-  if (!box_coord(b, blockIdx.x * (long long)blockDim.x + threadIdx.x, i, j, k)) return;
-  const long long p = pidx(d, i, j, k);
-  const long long s[3] = {1, d.sj, d.sk};
-  // adjoint of H^dir (components 1..4 carry the viscous flux)
-  dfl Hb[3][4];
-  for (int dir = 0; dir < 3; ++dir)
-    for (int m = 0; m < 4; ++m) Hb[dir][m] = df_of(0.5 * (a.acc[m + 1][p - s[dir]] - a.acc[m + 1][p + s[dir]]));
-  // forward viscous quantities
-  const double* f[4] = {w.u, w.v, w.w, w.T};
-  dfl S[3][3];
-  for (int dir = 0; dir < 3; ++dir)
-    for (int cc = 0; cc < 3; ++cc) S[dir][cc] = df_load(M.S[3 * dir + cc], p);
-  const dfl iV = df_load(M.invV, p);
-  dfl L[4][3];
-  for (int n = 0; n < 4; ++n) {
-    dfl dd[3];
-    for (int dir = 0; dir < 3; ++dir) dd[dir] = df_scale(df_sub(ld(f[n], p + s[dir]), ld(f[n], p - s[dir])), 0.5f);
-    for (int jj = 0; jj < 3; ++jj)
-      L[n][jj] = df_mul(iV, df_fma(S[2][jj], dd[2], df_fma(S[1][jj], dd[1], df_mul(S[0][jj], dd[0]))));
-  }
-  dfl Sij[3][3];
-  for (int x = 0; x < 3; ++x)
-    for (int y = 0; y < 3; ++y) Sij[x][y] = df_scale(df_add(L[x][y], L[y][x]), 0.5f);
-  const dfl div = df_add(df_add(Sij[0][0], Sij[1][1]), Sij[2][2]);
-  dfl SS = df_from(0.f);
-  for (int x = 0; x < 3; ++x)
-    for (int y = 0; y < 3; ++y) SS = df_fma(Sij[x][y], Sij[x][y], SS);
-  const dfl Smod = df_sqrt(df_scale(SS, 2.f));
-  const dfl mu = ld(w.mu, p);
-  const dfl csd = df_mul(c.C_s, df_load(M.Delta, p));
-  const dfl cs2 = df_mul(csd, csd);
-  const dfl rho = ld(qdf.q[0], p);
-  const dfl mu_sgs = df_mul(df_mul(rho, cs2), Smod);
-  const dfl mu_eff = df_add(mu, mu_sgs);
-  const dfl k_eff = df_add(df_mul(mu, c.k_lam), df_mul(mu_sgs, c.k_sgs));
-  const dfl d3 = df_mul(div, c.third);
-  const dfl m2 = df_scale(mu_eff, 2.f);
-  dfl dev[3][3];                                       // S_ij - delta_ij div/3
-  for (int x = 0; x < 3; ++x)
-    for (int y = 0; y < 3; ++y) dev[x][y] = x == y ? df_sub(Sij[x][y], d3) : Sij[x][y];
-  const dfl vel[3] = {ld(w.u, p), ld(w.v, p), ld(w.w, p)};
-  // reverse: F^dir_m = S^dir_j F_j,m ; H = E - F
-  dfl taub[3][3], ubd[3], keb = df_from(0.f), L3b[3];
-  for (int x = 0; x < 3; ++x) {
-    ubd[x] = df_from(0.f);
-    L3b[x] = df_from(0.f);
-    for (int y = 0; y < 3; ++y) taub[x][y] = df_from(0.f);
-  }
-  for (int jj = 0; jj < 3; ++jj) {
-    dfl Fb[4];
-    for (int m = 0; m < 4; ++m)
-      Fb[m] = df_neg(df_fma(S[2][jj], Hb[2][m], df_fma(S[1][jj], Hb[1][m], df_mul(S[0][jj], Hb[0][m]))));
-    for (int x = 0; x < 3; ++x) taub[x][jj] = df_add(taub[x][jj], Fb[x]);
-    const dfl e = Fb[3];
-    for (int x = 0; x < 3; ++x) {
-      ubd[x] = df_fma(e, df_mul(m2, dev[x][jj]), ubd[x]);         // e tau_x,jj
-      taub[x][jj] = df_fma(e, vel[x], taub[x][jj]);
-    }
-    keb = df_fma(e, L[3][jj], keb);
-    L3b[jj] = df_fma(e, k_eff, L3b[jj]);
-  }
-  dfl mueb = df_from(0.f), Sijb[3][3], tr = df_from(0.f);
-  for (int x = 0; x < 3; ++x)
-    for (int y = 0; y < 3; ++y) {
-      mueb = df_fma(taub[x][y], df_scale(dev[x][y], 2.f), mueb);
-      Sijb[x][y] = df_mul(m2, taub[x][y]);
-    }
-  for (int x = 0; x < 3; ++x) tr = df_add(tr, taub[x][x]);
-  const dfl divb = df_neg(df_mul(df_mul(mu_eff, df_scale(c.third, 2.f)), tr));
-  for (int x = 0; x < 3; ++x) Sijb[x][x] = df_add(Sijb[x][x], divb);
-  const dfl mub = df_add(df_mul(keb, c.k_lam), mueb);
-  const dfl musb = df_add(df_mul(keb, c.k_sgs), mueb);
-  const dfl rhob = df_mul(df_mul(musb, cs2), Smod);
-  const dfl Smodb = df_mul(df_mul(musb, rho), cs2);
-  const dfl SSb = df_gt0(Smod) ? df_mul(Smodb, df_rcp(Smod)) : df_from(0.f);
-  for (int x = 0; x < 3; ++x)
-    for (int y = 0; y < 3; ++y) Sijb[x][y] = df_fma(df_scale(Sij[x][y], 2.f), SSb, Sijb[x][y]);
-  dfl Lb[4][3];
-  for (int x = 0; x < 3; ++x)
-    for (int y = 0; y < 3; ++y) Lb[x][y] = df_scale(df_add(Sijb[x][y], Sijb[y][x]), 0.5f);
-  for (int y = 0; y < 3; ++y) Lb[3][y] = L3b[y];
-  for (int n = 0; n < 4; ++n)
-    for (int dir = 0; dir < 3; ++dir)
-      a.G[n][dir][p] =
-          df_to_f64(df_mul(iV, df_fma(S[dir][2], Lb[n][2], df_fma(S[dir][1], Lb[n][1], df_mul(S[dir][0], Lb[n][0])))));
-  for (int x = 0; x < 3; ++x) a.ubd[x][p] = df_to_f64(ubd[x]);
-  a.mub[p] = df_to_f64(mub);
-  a.rhob[p] = df_to_f64(rhob);
-  // pressure sensor nu = |N| / Dn
-  const dfl pc2 = df_scale(ld(w.p, p), 2.f);
-  for (int dir = 0; dir < 3; ++dir) {
-    const double nub = a.nb0[dir][p] + a.nb1[dir][p - s[dir]];
-    const dfl sum = df_add(ld(w.p, p + s[dir]), ld(w.p, p - s[dir]));
-    const dfl N = df_sub(sum, pc2), Dn = df_add(sum, pc2);
-    const dfl iD = df_rcp(Dn);
-    const dfl nu = df_mul(df_abs(N), iD);
-    const float sg = N.hi > 0.f ? 1.f : (N.hi < 0.f ? -1.f : 0.f);
-    const dfl nbD = df_mul(df_of(nub), iD);
-    a.cpm[dir][p] = df_to_f64(df_mul(nbD, df_sub(df_from(sg), nu)));
-    a.c0[dir][p] = df_to_f64(df_mul(nbD, df_scale(df_add(df_from(sg), nu), -2.f)));
-  }
-}
-
 // FP64 metrics -> double-float copies (every padded node).
 __global__ void k_metrics_df(Dims d, GridDev g, DFMetrics M) {
   const long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -437,39 +294,10 @@ __global__ void k_metrics_df(Dims d, GridDev g, DFMetrics M) {
   df_store(M.Delta, p, df_of(g.Delta[p]));
 }
 
-dfl pair_of(double x) {
-  const float h = (float)x;
-  return dfl{h, (float)(x - (double)h)};
-}
-
-ConstsDF make_cdf(const Consts& c) {
-  ConstsDF f;
-  f.gamma = pair_of(c.gamma);
-  f.gm1 = pair_of(c.gm1);
-  f.gm1_half = pair_of(c.gm1_half);
-  f.S_hat = pair_of(c.S_hat);
-  f.kappa2 = pair_of(c.kappa2);
-  f.kappa4 = pair_of(c.kappa4);
-  f.C_s = pair_of(c.C_s);
-  f.k_lam = pair_of(c.k_lam);
-  f.k_sgs = pair_of(c.k_sgs);
-  f.mu_sut = pair_of(c.mu_sut);
-  f.third = pair_of(1.0 / 3.0);
-  f.sigma_is_two_thirds = c.sigma_is_two_thirds;
-  f.sigma = c.sigma;
-  return f;
-}
 
 dim3 grid3(int ei, int ej, int ek) { return dim3((ei + BX - 1) / BX, (ej + BY - 1) / BY, ek); }
 
 }  // namespace
-
-cudaError_t adj_visc_df(const Dims& d, const Consts& c, const DFMetrics& M, const Work64& w, const QDF& qdf,
-                        const Adj64& a, cudaStream_t st) {
-  const long long n1 = (long long)(d.ni + 2) * (d.nj + 2) * (d.nk + 2);
-  k_adj_visc_df<<<blocks_for(n1, 256), 256, 0, st>>>(d, make_cdf(c), M, w, qdf, a);
-  return cudaGetLastError();
-}
 
 cudaError_t metrics_to_df(const Dims& d, const GridDev& g, const DFMetrics& M, cudaStream_t st) {
   k_metrics_df<<<blocks_for(d.Np, 256), 256, 0, st>>>(d, g, M);
