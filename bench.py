@@ -620,7 +620,7 @@ def main():
         ga, qa, pa = W.make_workload("jet128x96x64")
         grid_a = jz.Grid.from_workload(ga)
         # pair-form solver: states advanced, intermediates regenerated and the transposed passes
-        # run in pair arithmetic (adjoint arrays and gathers FP64)
+        # run in pair arithmetic (the running adjoint and the BC adjoints FP64)
         sa = jz.Solver(grid_a, pa, jz.JZ_PREC_FP64PAIR, stream=stream.cuda_stream)
         sa.set_state(torch.from_numpy(qa).cuda(), 0.0)
         amps = np.asarray(pa.forcing_amp)
@@ -639,7 +639,7 @@ def main():
         tot_a = sum(v[0] for v in prof_a.values())
         variants["adjoint"] = {
             "workload": "jet128x96x64", "steps": 200, "ckpt_every": 20, "r_obs": 0.75, "params": 32,
-            "forward": "pair arithmetic (FP64 state), also the regenerated intermediates and the transposed face, viscous and nodal passes; adjoint arrays, gathers and BC adjoints FP64",
+            "forward": "pair arithmetic (FP64 state), also the regenerated intermediates and the transposed passes and their intermediate adjoint arrays; running adjoint and BC adjoints FP64",
             "seconds_per_gradient": t_adj,
             "forward_equivalent_gpoint_stage_per_s": ga.npts * 5 * 200 / t_adj / 1e9,
             "J": Ja, "grad_inf": float(np.abs(ga_grad).max()),

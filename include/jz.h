@@ -66,7 +66,7 @@ extern "C" {
                                  jz_adjoint_step on such a solver advances
                                  the states, regenerates the intermediates and
                                  runs the transposed passes in pair arithmetic
-                                 (adjoint arrays, gathers and the boundary-
+                                 (the running adjoint and the boundary-
                                  condition adjoints in FP64).                 */
 
 #define JZ_N_MODES 8          /* azimuthal forcing modes m = 0..7            */

@@ -2,18 +2,36 @@
 // FP64 form and the structure of the reverse sweep): the face, viscous-and-sensor and nodal
 // passes in double-float arithmetic on the pair intermediates that the pair nodal and viscous
 // passes regenerated (u, v, w, T, p, mu, the sensors, Lambda, the pair copies of Q and of the
-// metrics).  The adjoint arrays stay FP64; the gathers sum them in FP64, and values cross
-// between the two representations by df_of and df_to_f64.
+// metrics).  The running adjoint lambda and Q^n's adjoint stay FP64 (as do the boundary-condition
+// adjoints and the observer); the intermediate adjoint arrays the transposed passes pass to one
+// another (alpha dt lambda / V, the face coefficients and sensor adjoints, the adjoints of the
+// gradients, of u, mu and rho) are double-float pairs in the same arrays, so the gathers of the
+// transposed nodal pass run on the FP32 pipes.
 #include "jz_adjgather.cuh"
 #include "jz_dfconsts.cuh"
 
 namespace jz {
 namespace {
 
+// Adjoint of the stage update: Qn_bar += lambda (FP64), acc = -alpha dt lambda / V as a pair, on
+// advanced real nodes (acc stays 0 elsewhere).
+__global__ void k_adj_update_df(Dims d, GridDev g, Adj64 a, double adt) {
+  Box b{0, 0, 0, d.ni, d.nj, d.nk};
+  int i, j, k;
+  if (!box_coord(b, blockIdx.x * (long long)blockDim.x + threadIdx.x, i, j, k)) return;
+  const long long p = pidx(d, i, j, k);
+  const bool adv = d.topo != JZ_TOPO_JET || (i >= 1 && i <= d.ni - 2 && j >= 1 && j <= d.nj - 2);
+  const double iV = g.invV[p];
+  for (int m = 0; m < 5; ++m) {
+    const double l = a.lam[m][p];
+    if (adv) a.qnbar[m][p] += l;
+    st(a.acc[m], p, adv ? df_of(-adt * l * iV) : df_from(0.f));
+  }
+}
+
 // Transposed dissipation faces of the discrete adjoint (jz_adjoint.cu, k_adj_faces) for a
-// pair-form solver, in double-float arithmetic on the pair copies of Q, the sensors and Lambda;
-// the differences of the FP64 adjoint array acc are formed in FP64 and converted, the outputs
-// converted back.  Faces n + 1/2, n in [-1, n_dir - 1].
+// pair-form solver, in double-float arithmetic on the pair copies of Q, the sensors and Lambda.
+// Faces n + 1/2, n in [-1, n_dir - 1].
 __global__ void k_adj_faces_df(Dims d, ConstsDF c, Work64 w, QDF qdf, Adj64 a) {
   Box b{-1, -1, -1, d.ni + 1, d.nj + 1, d.nk + 1};
   int i, j, k;
@@ -35,28 +53,27 @@ __global__ void k_adj_faces_df(Dims d, ConstsDF c, Work64 w, QDF qdf, Adj64 a) {
       const dfl q0 = ld(Q, p), q1 = ld(Q, p + sd), q2 = ld(Q, p + 2 * sd), qm = ld(Q, p - sd);
       const dfl d1 = df_sub(q1, q0);
       const dfl d3 = df_sub(df_add(df_sub(q2, df_mul_f(q1, 3.f)), df_mul_f(q0, 3.f)), qm);
-      const dfl Db = df_of(a.acc[m][p + sd] - a.acc[m][p]);
+      const dfl Db = df_sub(ld(a.acc[m], p + sd), ld(a.acc[m], p));
       lf = df_fma(Db, df_sub(df_mul(eps2, d1), df_mul(eps4, d3)), lf);
       const dfl DL = df_mul(Db, Lf);
       e2b = df_fma(DL, d1, e2b);
       e4b = df_sub(e4b, df_mul(DL, d3));
     }
-    a.ca2[dir][p] = df_to_f64(df_mul(Lf, eps2));
-    a.ca4[dir][p] = df_to_f64(df_mul(Lf, eps4));
+    st(a.ca2[dir], p, df_mul(Lf, eps2));
+    st(a.ca4[dir], p, df_mul(Lf, eps4));
     if (pos4) e2b = df_sub(e2b, e4b);
-    const double nub = df_to_f64(df_mul(c.kappa2, e2b));
-    a.nb0[dir][p] = first ? nub : 0.0;
-    a.nb1[dir][p] = first ? 0.0 : nub;
-    a.lfh[dir][p] = df_to_f64(df_scale(lf, 0.5f));
+    const dfl nub = df_mul(c.kappa2, e2b);
+    st(a.nb0[dir], p, first ? nub : df_from(0.f));
+    st(a.nb1[dir], p, first ? df_from(0.f) : nub);
+    st(a.lfh[dir], p, df_scale(lf, 0.5f));
   }
 }
 
 // Transposed viscous pass and pressure sensor of the discrete adjoint (jz_adjoint.cu, k_adj_visc)
 // for a pair-form solver: the same reverse sweep through gradients, strain rate, eddy viscosity,
 // stresses, heat flux and sensors, in double-float arithmetic on the pair intermediates the pair
-// passes regenerated (u, v, w, T, p, mu, the pair copies of Q and of the metrics).  The adjoint
-// arrays stay FP64: the incoming differences are formed in FP64 and converted, the outputs
-// converted back.  Nodes within one layer of the real region.
+// passes regenerated (u, v, w, T, p, mu, the pair copies of Q and of the metrics).  Nodes within
+// one layer of the real region.
 __global__ void k_adj_visc_df(Dims d, ConstsDF c, DFMetrics M, Work64 w, QDF qdf, Adj64 a) {
   Box b{-1, -1, -1, d.ni + 2, d.nj + 2, d.nk + 2};
   int i, j, k;
@@ -66,7 +83,7 @@ __global__ void k_adj_visc_df(Dims d, ConstsDF c, DFMetrics M, Work64 w, QDF qdf
   // adjoint of H^dir (components 1..4 carry the viscous flux)
   dfl Hb[3][4];
   for (int dir = 0; dir < 3; ++dir)
-    for (int m = 0; m < 4; ++m) Hb[dir][m] = df_of(0.5 * (a.acc[m + 1][p - s[dir]] - a.acc[m + 1][p + s[dir]]));
+    for (int m = 0; m < 4; ++m) Hb[dir][m] = df_scale(df_sub(ld(a.acc[m + 1], p - s[dir]), ld(a.acc[m + 1], p + s[dir])), 0.5f);
   // forward viscous quantities
   const double* f[4] = {w.u, w.v, w.w, w.T};
   dfl S[3][3];
@@ -143,48 +160,110 @@ __global__ void k_adj_visc_df(Dims d, ConstsDF c, DFMetrics M, Work64 w, QDF qdf
   for (int y = 0; y < 3; ++y) Lb[3][y] = L3b[y];
   for (int n = 0; n < 4; ++n)
     for (int dir = 0; dir < 3; ++dir)
-      a.G[n][dir][p] =
-          df_to_f64(df_mul(iV, df_fma(S[dir][2], Lb[n][2], df_fma(S[dir][1], Lb[n][1], df_mul(S[dir][0], Lb[n][0])))));
-  for (int x = 0; x < 3; ++x) a.ubd[x][p] = df_to_f64(ubd[x]);
-  a.mub[p] = df_to_f64(mub);
-  a.rhob[p] = df_to_f64(rhob);
+      st(a.G[n][dir], p, df_mul(iV, df_fma(S[dir][2], Lb[n][2], df_fma(S[dir][1], Lb[n][1], df_mul(S[dir][0], Lb[n][0])))));
+  for (int x = 0; x < 3; ++x) st(a.ubd[x], p, ubd[x]);
+  st(a.mub, p, mub);
+  st(a.rhob, p, rhob);
   // pressure sensor nu = |N| / Dn
   const dfl pc2 = df_scale(ld(w.p, p), 2.f);
   for (int dir = 0; dir < 3; ++dir) {
-    const double nub = a.nb0[dir][p] + a.nb1[dir][p - s[dir]];
+    const dfl nub = df_add(ld(a.nb0[dir], p), ld(a.nb1[dir], p - s[dir]));
     const dfl sum = df_add(ld(w.p, p + s[dir]), ld(w.p, p - s[dir]));
     const dfl N = df_sub(sum, pc2), Dn = df_add(sum, pc2);
     const dfl iD = df_rcp(Dn);
     const dfl nu = df_mul(df_abs(N), iD);
     const float sg = N.hi > 0.f ? 1.f : (N.hi < 0.f ? -1.f : 0.f);
-    const dfl nbD = df_mul(df_of(nub), iD);
-    a.cpm[dir][p] = df_to_f64(df_mul(nbD, df_sub(df_from(sg), nu)));
-    a.c0[dir][p] = df_to_f64(df_mul(nbD, df_scale(df_add(df_from(sg), nu), -2.f)));
+    const dfl nbD = df_mul(nub, iD);
+    st(a.cpm[dir], p, df_mul(nbD, df_sub(df_from(sg), nu)));
+    st(a.c0[dir], p, df_mul(nbD, df_scale(df_add(df_from(sg), nu), -2.f)));
   }
 }
 
 
-// Transposed nodal pass (jz_adjoint.cu, k_adj_nodal) for a pair-form solver: the gathers in
-// FP64, then the reverse of the anisotropic spectral radii, the inviscid fluxes, Sutherland's
-// law and the primitives in double-float arithmetic on the pair copies of Q and the metrics.
-// Every padded node.  Four 128-thread blocks per SM (128 registers, some spilled): 1.79 s per
-// 200-step gradient on 128 x 96 x 64, against 1.83 at three (168) and 1.91 at two (254).
+// A pair adjoint array at (i, j, k) + offset along dir, 0 outside the padded box.
+__device__ __forceinline__ dfl nbp(const Dims& d, const double* f, int i, int j, int k, int dir, int off) {
+  int ii = i, jj = j, kk = k;
+  if (dir == 0) ii += off; else if (dir == 1) jj += off; else kk += off;
+  return in_box(d, ii, jj, kk) ? ld(f, pidx(d, ii, jj, kk)) : df_from(0.f);
+}
+
+// The gathers of the transposed nodal pass (as nodal_gathers, jz_adjgather.cuh) on the pair
+// adjoint arrays, summed in double-float.
+struct NodalGathersDF {
+  dfl fb[4], pb, Eb[3][5], Lamb[3], qb[5], mub;
+};
+__device__ __forceinline__ void nodal_gathers_df(const Dims& d, const Adj64& a, int i, int j, int k,
+                                                 NodalGathersDF& G) {
+#pragma unroll
+  for (int n = 0; n < 4; ++n) {
+    dfl v = n < 3 ? nbp(d, a.ubd[n], i, j, k, 0, 0) : df_from(0.f);
+#pragma unroll
+    for (int dir = 0; dir < 3; ++dir)
+      v = df_add(v, df_scale(df_sub(nbp(d, a.G[n][dir], i, j, k, dir, -1), nbp(d, a.G[n][dir], i, j, k, dir, 1)), 0.5f));
+    G.fb[n] = v;
+  }
+  G.pb = df_from(0.f);
+#pragma unroll
+  for (int dir = 0; dir < 3; ++dir)
+    G.pb = df_add(G.pb, df_add(df_add(nbp(d, a.c0[dir], i, j, k, 0, 0), nbp(d, a.cpm[dir], i, j, k, dir, -1)),
+                               nbp(d, a.cpm[dir], i, j, k, dir, 1)));
+#pragma unroll
+  for (int dir = 0; dir < 3; ++dir) {
+#pragma unroll
+    for (int m = 0; m < 5; ++m)
+      G.Eb[dir][m] = df_scale(df_sub(nbp(d, a.acc[m], i, j, k, dir, -1), nbp(d, a.acc[m], i, j, k, dir, 1)), 0.5f);
+    G.Lamb[dir] = df_add(nbp(d, a.lfh[dir], i, j, k, 0, 0), nbp(d, a.lfh[dir], i, j, k, dir, -1));
+  }
+#pragma unroll
+  for (int m = 0; m < 5; ++m) G.qb[m] = df_from(0.f);
+#pragma unroll
+  for (int dir = 0; dir < 3; ++dir) {
+    dfl c2[4], c4[4];              // faces n-2, n-1, n, n+1
+#pragma unroll
+    for (int o = 0; o < 4; ++o) {
+      c2[o] = nbp(d, a.ca2[dir], i, j, k, dir, o - 2);
+      c4[o] = nbp(d, a.ca4[dir], i, j, k, dir, o - 2);
+    }
+#pragma unroll
+    for (int m = 0; m < 5; ++m) {
+      const dfl am2 = nbp(d, a.acc[m], i, j, k, dir, -2), am1 = nbp(d, a.acc[m], i, j, k, dir, -1),
+                a0 = nbp(d, a.acc[m], i, j, k, 0, 0), ap1 = nbp(d, a.acc[m], i, j, k, dir, 1),
+                ap2 = nbp(d, a.acc[m], i, j, k, dir, 2);
+      const dfl D0 = df_sub(am1, am2), D1 = df_sub(a0, am1), D2 = df_sub(ap1, a0), D3 = df_sub(ap2, ap1);
+      // -D0 c4(n-2) + D1 (c2(n-1) + 3 c4(n-1)) - D2 (c2(n) + 3 c4(n)) + D3 c4(n+1)
+      dfl v = df_sub(df_mul(D3, c4[3]), df_mul(D0, c4[0]));
+      v = df_fma(D1, df_add(c2[1], df_mul_f(c4[1], 3.f)), v);
+      v = df_sub(v, df_mul(D2, df_add(c2[2], df_mul_f(c4[2], 3.f))));
+      G.qb[m] = df_add(G.qb[m], v);
+    }
+  }
+  G.qb[0] = df_add(G.qb[0], nbp(d, a.rhob, i, j, k, 0, 0));
+  G.mub = nbp(d, a.mub, i, j, k, 0, 0);
+}
+
+// Transposed nodal pass (jz_adjoint.cu, k_adj_nodal) for a pair-form solver: the gathers, then
+// the reverse of the anisotropic spectral radii, the inviscid fluxes, Sutherland's law and the
+// primitives, all in double-float arithmetic (the gathers on the pair adjoint arrays).
+// Every padded node.  Three 128-thread blocks per SM (168 registers): 1.49 s per 200-step
+// gradient on 128 x 96 x 64, against 1.51 at four (128, spilling) and 1.55 at two (188).
 constexpr int kTPBN = 128;
-__global__ void __launch_bounds__(kTPBN, 4) k_adj_nodal_df(Dims d, ConstsDF c, DFMetrics M, QDF qdf, Adj64 a) {
+__global__ void __launch_bounds__(kTPBN, 3) k_adj_nodal_df(Dims d, ConstsDF c, DFMetrics M, QDF qdf, Adj64 a) {
   Box b{-kG, -kG, -kG, d.ni + 2 * kG, d.nj + 2 * kG, d.nk + 2 * kG};
   int i, j, k;
   if (!box_coord(b, blockIdx.x * (long long)blockDim.x + threadIdx.x, i, j, k)) return;
   const long long p = pidx(d, i, j, k);
-  NodalGathers G;
-  nodal_gathers(d, a, i, j, k, G);
-  dfl ub[3] = {df_of(G.fb[0]), df_of(G.fb[1]), df_of(G.fb[2])};
-  dfl Tb = df_of(G.fb[3]);
-  dfl pb = df_of(G.pb);
+  NodalGathersDF G;
+  nodal_gathers_df(d, a, i, j, k, G);
+  dfl ub[3] = {G.fb[0], G.fb[1], G.fb[2]};
+  dfl Tb = G.fb[3];
+  dfl pb = G.pb;
   dfl qb[5];
-  for (int m = 0; m < 5; ++m) qb[m] = df_of(G.qb[m]);
-  const dfl mub = df_of(G.mub);
+#pragma unroll
+  for (int m = 0; m < 5; ++m) qb[m] = G.qb[m];
+  const dfl mub = G.mub;
   // forward nodal quantities
   dfl Q[5];
+#pragma unroll
   for (int m = 0; m < 5; ++m) Q[m] = ld(qdf.q[m], p);
   const dfl rho = Q[0];
   const dfl ir = df_rcp(rho);
@@ -195,17 +274,20 @@ __global__ void __launch_bounds__(kTPBN, 4) k_adj_nodal_df(Dims d, ConstsDF c, D
   const dfl iTS = df_rcp(df_add(T, c.S_hat));
   const dfl mu = df_mul(df_mul(c.mu_sut, df_mul(T, aa)), iTS);
   dfl Sv[3][3], Smag[3], U[3], lam[3];
+#pragma unroll
   for (int dir = 0; dir < 3; ++dir) {
+#pragma unroll
     for (int cc = 0; cc < 3; ++cc) Sv[dir][cc] = df_load(M.S[3 * dir + cc], p);
     Smag[dir] = df_load(M.Smag[dir], p);
     U[dir] = df_fma(Sv[dir][2], u[2], df_fma(Sv[dir][1], u[1], df_mul(Sv[dir][0], u[0])));
     lam[dir] = df_fma(aa, Smag[dir], df_abs(U[dir]));
   }
   // anisotropic scaling Lambda_d = lam_d + lo_d (hi_e + hi_f)
-  const dfl Lamb[3] = {df_of(G.Lamb[0]), df_of(G.Lamb[1]), df_of(G.Lamb[2])};
+  const dfl Lamb[3] = {G.Lamb[0], G.Lamb[1], G.Lamb[2]};
   dfl lamb[3] = {Lamb[0], Lamb[1], Lamb[2]};
   {
     dfl lo[3], hi[3], dlo[3], dhi[3];
+#pragma unroll
     for (int dd = 0; dd < 3; ++dd) {
       if (c.sigma_is_two_thirds) {
         df_cbrt_pair(lam[dd], lo[dd], hi[dd]);                       // lam^(1/3), lam^(2/3)
@@ -223,27 +305,31 @@ __global__ void __launch_bounds__(kTPBN, 4) k_adj_nodal_df(Dims d, ConstsDF c, D
       }
     }
     dfl lob[3], hib[3];
+#pragma unroll
     for (int dd = 0; dd < 3; ++dd) lob[dd] = hib[dd] = df_from(0.f);
     const int e1[3] = {1, 0, 0}, e2[3] = {2, 2, 1};
+#pragma unroll
     for (int dd = 0; dd < 3; ++dd) {
       lob[dd] = df_fma(Lamb[dd], df_add(hi[e1[dd]], hi[e2[dd]]), lob[dd]);
       const dfl Ll = df_mul(Lamb[dd], lo[dd]);
       hib[e1[dd]] = df_add(hib[e1[dd]], Ll);
       hib[e2[dd]] = df_add(hib[e2[dd]], Ll);
     }
+#pragma unroll
     for (int dd = 0; dd < 3; ++dd) lamb[dd] = df_fma(hib[dd], dhi[dd], df_fma(lob[dd], dlo[dd], lamb[dd]));
   }
   dfl ab = df_from(0.f);
   const dfl h0 = df_add(Q[4], pr);
+#pragma unroll
   for (int dir = 0; dir < 3; ++dir) {
-    const dfl E[5] = {df_of(G.Eb[dir][0]), df_of(G.Eb[dir][1]), df_of(G.Eb[dir][2]), df_of(G.Eb[dir][3]),
-                      df_of(G.Eb[dir][4])};
+    const dfl E[5] = {G.Eb[dir][0], G.Eb[dir][1], G.Eb[dir][2], G.Eb[dir][3], G.Eb[dir][4]};
     const float sg = U[dir].hi > 0.f ? 1.f : (U[dir].hi < 0.f ? -1.f : 0.f);
     dfl Ub = df_mul_f(lamb[dir], sg);
     ab = df_fma(lamb[dir], Smag[dir], ab);
     // E = [rho U, m_i U + p S_i, (e + p) U]
     qb[0] = df_fma(E[0], U[dir], qb[0]);
     Ub = df_fma(E[0], rho, Ub);
+#pragma unroll
     for (int x = 0; x < 3; ++x) {
       qb[1 + x] = df_fma(E[1 + x], U[dir], qb[1 + x]);
       Ub = df_fma(E[1 + x], Q[1 + x], Ub);
@@ -252,6 +338,7 @@ __global__ void __launch_bounds__(kTPBN, 4) k_adj_nodal_df(Dims d, ConstsDF c, D
     qb[4] = df_fma(E[4], U[dir], qb[4]);
     pb = df_fma(E[4], U[dir], pb);
     Ub = df_fma(E[4], h0, Ub);
+#pragma unroll
     for (int x = 0; x < 3; ++x) ub[x] = df_fma(Ub, Sv[dir][x], ub[x]);
   }
   // Sutherland mu(T): d mu / dT = mu (1.5/T - 1/(T + S))
@@ -262,20 +349,29 @@ __global__ void __launch_bounds__(kTPBN, 4) k_adj_nodal_df(Dims d, ConstsDF c, D
   // reverse of u_i = m_i / rho, p = (gamma-1)(e - m.u/2)
   qb[4] = df_fma(c.gm1, pb, qb[4]);
   const dfl keb = df_scale(df_neg(df_mul(c.gm1, pb)), 0.5f);      // half the adjoint of m.u
+#pragma unroll
   for (int x = 0; x < 3; ++x) {
     qb[1 + x] = df_fma(keb, u[x], qb[1 + x]);
     ub[x] = df_fma(keb, Q[1 + x], ub[x]);
   }
   dfl sum = df_from(0.f);
+#pragma unroll
   for (int x = 0; x < 3; ++x) {
     qb[1 + x] = df_fma(ub[x], ir, qb[1 + x]);
     sum = df_fma(ub[x], u[x], sum);
   }
   qb[0] = df_sub(qb[0], df_mul(sum, ir));
+#pragma unroll
   for (int m = 0; m < 5; ++m) a.lam[m][p] = df_to_f64(qb[m]);
 }
 
 }  // namespace
+
+cudaError_t adj_update_df(const Dims& d, const GridDev& g, const Adj64& a, double adt, cudaStream_t st) {
+  const long long nr = (long long)d.ni * d.nj * d.nk;
+  k_adj_update_df<<<blocks_for(nr, 256), 256, 0, st>>>(d, g, a, adt);
+  return cudaGetLastError();
+}
 
 cudaError_t adj_nodal_df(const Dims& d, const Consts& c, const DFMetrics& M, const QDF& qdf, const Adj64& a,
                          cudaStream_t st) {

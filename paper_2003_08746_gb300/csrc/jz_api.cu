@@ -1003,7 +1003,8 @@ int jz_adjoint_step(jz_solver* s, const double* forcing_amps, int nsteps, int ck
       }
       for (int l = 4; l >= 0; --l) {
         JZ_RUN(JZ_PROF_ADJOINT, jz::adj_bcs(d, s->c, g, s->in, *st[l + 1], a, tn + kAlpha[l] * dt, s->st));
-        JZ_RUN(JZ_PROF_ADJOINT, jz::adj_update(d, g, a, kAlpha[l] * dt, s->st));
+        JZ_RUN(JZ_PROF_ADJOINT, s->pair ? jz::adj_update_df(d, g, a, kAlpha[l] * dt, s->st)
+                                        : jz::adj_update(d, g, a, kAlpha[l] * dt, s->st));
         // the forward intermediates the transposed passes read, regenerated in the solver's form
         if (s->pair) {
           JZ_RUN(JZ_PROF_NODAL, jz::nodal_df(d, s->c, s->mdf, s->w, s->qdf, *st[l], s->st));

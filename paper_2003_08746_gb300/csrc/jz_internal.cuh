@@ -376,6 +376,8 @@ cudaError_t adj_faces_df(const Dims& d, const Consts& c, const Work64& w, const 
                          cudaStream_t st);
 cudaError_t adj_nodal_df(const Dims& d, const Consts& c, const DFMetrics& M, const QDF& qdf, const Adj64& a,
                          cudaStream_t st);
+// pair-form solver: acc stored as double-float pairs (read by the pair transposed passes only)
+cudaError_t adj_update_df(const Dims& d, const GridDev& g, const Adj64& a, double adt, cudaStream_t st);
 cudaError_t adj_add_qn(const Dims& d, const Adj64& a, cudaStream_t st);
 cudaError_t adj_bcs(const Dims& d, const Consts& c, const GridDev& g, const Inflow& in, const State& q,
                     const Adj64& a, double ts, cudaStream_t st);
