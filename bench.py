@@ -386,6 +386,8 @@ def main():
     ap.add_argument("--no-mesh-i", action="store_true", help="skip the FP32-flux line on the paper's mesh I")
     ap.add_argument("--adjoint-only", action="store_true", help="one adjoint gradient over --steps steps "
                     "on the 128 x 96 x 64 jet (profiling runs)")
+    ap.add_argument("--adjoint-form", choices=("pair", "fp64"), default="pair",
+                    help="solver form of --adjoint-only (default: the FP64 form in pair arithmetic)")
     ap.add_argument("--configs-table", action="store_true", help="GPU FP64 / FP32-flux and oracle 1-thread / "
                     "all-thread rates for every workload of the config list (one JSON line each)")
     ap.add_argument("--paper-meshes", default="", help="comma list of the paper's meshes (A..I) to time "
@@ -416,11 +418,12 @@ def main():
         # one gradient on the 128 x 96 x 64 jet, args.steps steps, checkpoints every 10 (profiling runs)
         ga, qa, pa = W.make_workload("jet128x96x64")
         grid_a = jz.Grid.from_workload(ga)
-        sa = jz.Solver(grid_a, pa, jz.JZ_PREC_FP64)
+        sa = jz.Solver(grid_a, pa, jz.JZ_PREC_FP64PAIR if args.adjoint_form == "pair" else jz.JZ_PREC_FP64)
         sa.set_state(torch.from_numpy(qa).cuda(), 0.0)
         t0 = time.perf_counter()
         Ja, ga_grad = jz.jz_adjoint_step(sa.h, np.asarray(pa.forcing_amp), args.steps, 10, 0.75)
-        print(json.dumps({"form": "adjoint", "workload": "jet128x96x64", "steps": args.steps, "ckpt_every": 10,
+        print(json.dumps({"form": "adjoint", "solver": args.adjoint_form, "workload": "jet128x96x64",
+                          "steps": args.steps, "ckpt_every": 10,
                           "seconds": time.perf_counter() - t0, "J": Ja, "grad_inf": float(np.abs(ga_grad).max())}),
               flush=True)
         sa.close()
