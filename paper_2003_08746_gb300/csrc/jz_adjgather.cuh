@@ -1,7 +1,7 @@
-// Gathers of the transposed nodal pass of the discrete adjoint, shared by its FP64 form
-// (jz_adjoint.cu) and its pair form (jz_adjointdf.cu): what node (i, j, k) receives from the
-// transposed viscous, sensor, inviscid-flux, spectral-radius and dissipation terms of its
-// neighbours, summed in FP64.
+// Gathers of the transposed nodal pass of the discrete adjoint (jz_adjoint.cu): what node
+// (i, j, k) receives from the transposed viscous, sensor, inviscid-flux, spectral-radius and
+// dissipation terms of its neighbours, summed in FP64.  The pair form (jz_adjointdf.cu) shares
+// the padded-box test and sums the same terms in double-float on its pair arrays.
 #pragma once
 
 #include "jz_internal.cuh"
